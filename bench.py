@@ -1,0 +1,458 @@
+#!/usr/bin/env python3
+"""Benchmark of the TSM2R / TSM2L library on GB300.
+
+Workload (one "step"): the binary32 sweep of the paper's shapes (Sec. 4.1):
+TSM2R with A n x n, n in {10240, 20480, 30720}, times B n x k, k in
+{2, 4, 8, 16}; and TSM2L with A m x n, m in {2^20, 2^23}, n in {8, 16, 32},
+times B n x n.  Entries are uniform in [-1, 1) from the splitmix64 generator,
+generated in device memory.  Every launch is preceded by an L2 flush (a
+memset of twice the L2 size) and timed on its stream with CUDA events; the
+step time is the sum of the 18 kernel durations.
+
+Metric: achieved HBM bandwidth, algorithmic bytes s*(m n + n k + m k) per
+multiply divided by kernel time, in GB/s (whole job: summed over ranks).
+
+Also reported on the same line: the binary64 sweep (compute-bound on GB300's
+FP64 units, so reported against the FP64 roof), cuBLAS GEMM on the same
+operands (comparator), an end-to-end figure through the public C ABI with
+host buffers, SM clocks sampled during the timed region, the roofline of the
+dominant kernel, and the CPU oracle timed on the host cores.
+
+``--impl reference`` times the CPU oracle (the reference implementation of
+the definition) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+R_SIZES = [10240, 20480, 30720]
+R_KS = [2, 4, 8, 16]
+L_MS = [2 ** 20, 2 ** 23]
+L_NS = [8, 16, 32]
+WORKLOAD = ("tsm2 sweep: TSM2R n x n * n x k, n in {10240,20480,30720}, k in {2,4,8,16}; "
+            "TSM2L m x n * n x n, m in {2^20,2^23}, n in {8,16,32}; uniform[-1,1) seed 0")
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 nominal FP64 (no FP64 tensor-core speed-up)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def cases(dtype_bytes):
+    out = []
+    for n in R_SIZES:
+        for k in R_KS:
+            out.append(("r", n, n, k))
+    for m in L_MS:
+        for n in L_NS:
+            out.append(("l", m, n, n))
+    return [(op, m, n, k, dtype_bytes) for (op, m, n, k) in out]
+
+
+def alg_bytes(m, n, k, es):
+    return es * (m * n + n * k + m * k)
+
+
+def launches_per_call(op, k):
+    kc = 32 if op == "l" else 16
+    return (k + kc - 1) // kc
+
+
+def src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2002_03258_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_record(config_name, workload_key):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        j = json.load(open(p))
+    except Exception:
+        return None
+    rec = j.get(config_name, {}).get(workload_key)
+    if not rec or rec.get("src_hash") != src_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"tsm2_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        self.t0 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        loaded = [x for x in sm if x > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle arm (reference arm and cpu_baseline)
+
+def oracle_sample_run(dtype_name, steps, warmup, budget_s=20.0):
+    """Time the CPU oracle on a bounded row sample of every case of the sweep.
+
+    Returns (GB/s, description, cores, seconds per step)."""
+    import numpy as np
+
+    import oracle
+    import tsm2_inputs as ti
+    dt = np.float32 if dtype_name == "f32" else np.float64
+    es = 4 if dt == np.float32 else 8
+    cores = os.cpu_count() or 1
+    samples = []
+    for op, m, n, k, _ in cases(es):
+        rows = max(64, min(m, (1 << 21) // n))  # about 2M elements of A per case
+        ridx = np.arange(rows)
+        A = ti.uniform_pm1(0, ti.MID_A, m, n, dt, row_idx=ridx)
+        B = ti.uniform_pm1(0, ti.MID_B, n, k, dt)
+        samples.append((A, B, alg_bytes(rows, n, k, es)))
+    tot_bytes = sum(s[2] for s in samples)
+    for _ in range(max(0, warmup)):
+        for A, B, _ in samples[:1]:
+            oracle.gemm_threaded(A, B, cores)
+    times = []
+    for _ in range(max(1, steps)):
+        t0 = time.perf_counter()
+        for A, B, _ in samples:
+            oracle.gemm_threaded(A, B, cores)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    desc = (f"first max(64, 2^21/n) rows of A for each of the {len(samples)} sweep cases "
+            f"({tot_bytes / 1e6:.0f} MB algorithmic per step), oracle.gemm_threaded on {cores} threads")
+    return tot_bytes / t / 1e9, desc, cores, t
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    steps = max(1, args.steps)
+    value, desc, cores, t = oracle_sample_run("f32", steps, min(args.warmup, 1))
+    line = {
+        "impl": "reference", "metric": "TSM2R/TSM2L achieved HBM GB/s (binary32 sweep)", "value": round(value, 4),
+        "unit": "GB/s", "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": round(t * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (row sample, CPU)", "sample": desc},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as ge
+    world, rank, local = dist_setup()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ge.build()
+    import paper_2002_03258_gb300 as pkg
+    import tsm2_inputs as ti
+    lib = pkg.lib()
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+
+    props = torch.cuda.get_device_properties(dev)
+    l2 = getattr(props, "L2_cache_size", 128 << 20) or (128 << 20)
+    flush = torch.empty(2 * l2, dtype=torch.uint8, device=dev)
+
+    def l2_flush():
+        flush.zero_()
+
+    def make_sweep(es, seed):
+        tdt = torch.float32 if es == 4 else torch.float64
+        suf = "s" if es == 4 else "d"
+        fill = getattr(lib, f"tsm2_fill_uniform_{suf}")
+        bufs = {}
+        work = []
+        for op, m, n, k, _ in cases(es):
+            keyA = ("A", op, m, n)
+            if keyA not in bufs:
+                t = torch.empty((n, m), dtype=tdt, device=dev).t()
+                pkg.check(fill(m, n, seed, ti.MID_A, t.data_ptr(), m, sh))
+                bufs[keyA] = t
+            kmax = 16 if op == "r" else n
+            keyB = ("B", op, n, kmax)
+            if keyB not in bufs:
+                t = torch.empty((kmax, n), dtype=tdt, device=dev).t()
+                pkg.check(fill(n, kmax, seed, ti.MID_B, t.data_ptr(), n, sh))
+                bufs[keyB] = t
+            keyC = ("C", op, m, kmax)
+            if keyC not in bufs:
+                bufs[keyC] = torch.empty((kmax, m), dtype=tdt, device=dev).t()
+            fn = getattr(pkg, f"tsm2{op}_{suf}")
+            work.append(dict(op=op, m=m, n=n, k=k, es=es, fn=fn, A=bufs[keyA], B=bufs[keyB], C=bufs[keyC],
+                             bytes=alg_bytes(m, n, k, es), flops=2 * m * n * k))
+        return work, bufs
+
+    def call(w, s=sh):
+        return w["fn"](w["m"], w["n"], w["k"], w["A"].data_ptr(), w["m"], w["B"].data_ptr(), w["n"],
+                       w["C"].data_ptr(), w["m"], s)
+
+    def timed_steps(work, steps, warmup):
+        for _ in range(warmup):
+            for w in work:
+                l2_flush()
+                pkg.check(call(w))
+        torch.cuda.synchronize()
+        pkg.check(pkg.tsm2_get_device_status(sh))
+        evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in work]
+               for _ in range(steps)]
+        configs = {}
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_region0 = time.perf_counter()
+        for s in range(steps):
+            for i, w in enumerate(work):
+                l2_flush()
+                evs[s][i][0].record(stream)
+                pkg.check(call(w))
+                evs[s][i][1].record(stream)
+                configs[i] = pkg.tsm2_last_config()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        wall = time.perf_counter() - t_region0
+        pkg.check(pkg.tsm2_get_device_status(sh))
+        per = [[evs[s][i][0].elapsed_time(evs[s][i][1]) for i in range(len(work))] for s in range(steps)]
+        return per, configs, wall
+
+    peak_hbm, peak_kind = measured_peaks()
+    clocks = ClockSampler(local)
+
+    # ---- binary32 sweep: the headline -------------------------------------------------
+    work32, bufs32 = make_sweep(4, 0)
+    torch.cuda.synchronize()
+    clocks.start()
+    per, configs, wall = timed_steps(work32, args.steps, args.warmup)
+    clock_rec = clocks.stop()
+    step_ms = [sum(row) for row in per]
+    mean_step_ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([mean_step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mean_step_ms = float(t.item())
+    step_bytes = sum(w["bytes"] for w in work32)
+    value = world * step_bytes / (mean_step_ms * 1e-3) / 1e9
+    case_rows = []
+    for i, w in enumerate(work32):
+        ms = statistics.mean(per[s][i] for s in range(args.steps))
+        case_rows.append({"op": "tsm2" + w["op"], "m": w["m"], "n": w["n"], "k": w["k"], "ms": round(ms, 4),
+                          "gbs": round(w["bytes"] / (ms * 1e-3) / 1e9, 1),
+                          "frac_hbm": round(w["bytes"] / (ms * 1e-3) / 1e9 / peak_hbm, 3),
+                          "config": configs.get(i)})
+    dom = max(range(len(work32)), key=lambda i: case_rows[i]["ms"])
+    dw = work32[dom]
+    dom_ms = case_rows[dom]["ms"]
+    achieved = dw["bytes"] / (dom_ms * 1e-3) / 1e9
+    wkey = f"{dw['op']}_{dw['m']}x{dw['n']}x{dw['k']}_f32"
+    traffic = traffic_record(configs.get(dom), wkey)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak_hbm, "unit": "GB/s",
+                "frac": round(achieved / peak_hbm, 4), "traffic": traffic,
+                "kernel": configs.get(dom), "workload": wkey, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": dw["bytes"]}
+
+    # ---- cuBLAS comparator on the same operands (not timed in the step) -----------------
+    cublas = []
+    if not args.no_cublas:
+        for i, w in enumerate(work32):
+            A, B = w["A"], w["B"][:, :w["k"]]
+            out = torch.empty((w["k"], w["m"]), dtype=A.dtype, device=dev).t()
+            torch.matmul(A, B, out=out)
+            ts = []
+            for _ in range(3):
+                l2_flush()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                torch.matmul(A, B, out=out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            case_rows[i]["cublas_ms"] = round(ms, 4)
+            case_rows[i]["speedup_vs_cublas"] = round(ms / case_rows[i]["ms"], 3)
+            del out
+
+    # ---- binary64 sweep (FP64 ALU bound) ----------------------------------------------------
+    fp64 = None
+    if not args.no_fp64:
+        work64, bufs64 = make_sweep(8, 0)
+        per64, configs64, _ = timed_steps(work64, max(1, min(args.steps, 3)), min(args.warmup, 3))
+        ms64 = statistics.mean(sum(r) for r in per64)
+        bytes64 = sum(w["bytes"] for w in work64)
+        flops64 = sum(w["flops"] for w in work64)
+        d64 = max(range(len(work64)), key=lambda i: per64[0][i])
+        d64_ms = statistics.mean(r[d64] for r in per64)
+        tfl = work64[d64]["flops"] / (d64_ms * 1e-3) / 1e12
+        fp64 = {"value": round(bytes64 / (ms64 * 1e-3) / 1e9, 1), "unit": "GB/s", "ms_per_step": round(ms64, 3),
+                "tflops": round(flops64 / (ms64 * 1e-3) / 1e12, 3),
+                "roofline": {"bound": "alu", "achieved": round(tfl, 3), "peak": FP64_NOMINAL_TFLOPS,
+                             "unit": "TFLOP/s", "frac": round(tfl / FP64_NOMINAL_TFLOPS, 4),
+                             "kernel": configs64.get(d64), "peak_kind": "nominal FP64 (recipe)",
+                             "workload": f"{work64[d64]['op']}_{work64[d64]['m']}x{work64[d64]['n']}x{work64[d64]['k']}_f64"},
+                "cases": [{"op": "tsm2" + w["op"], "m": w["m"], "n": w["n"], "k": w["k"],
+                           "ms": round(statistics.mean(r[i] for r in per64), 4),
+                           "tflops": round(w["flops"] / (statistics.mean(r[i] for r in per64) * 1e-3) / 1e12, 3)}
+                          for i, w in enumerate(work64)]}
+        del bufs64, work64
+        torch.cuda.empty_cache()
+
+    # ---- end to end through the C ABI with host buffers --------------------------------------
+    h_in, h_out = [], []
+    for w in work32:
+        hA = torch.empty((w["n"], w["m"]), dtype=w["A"].dtype, pin_memory=True).t()
+        hA.copy_(w["A"])
+        hB = torch.empty((w["B"].shape[1], w["n"]), dtype=w["A"].dtype, pin_memory=True).t()
+        hB.copy_(w["B"])
+        hC = torch.empty((w["k"], w["m"]), dtype=w["A"].dtype, pin_memory=True).t()
+        h_in.append((hA, hB))
+        h_out.append(hC)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 5))
+    h2d = sum(w["A"].numel() * w["es"] + w["n"] * w["k"] * w["es"] for w in work32)
+    d2h = sum(w["m"] * w["k"] * w["es"] for w in work32)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_start.record(stream)
+    for _ in range(e2e_steps):
+        for (hA, hB), hC, w in zip(h_in, h_out, work32):
+            w["A"].copy_(hA, non_blocking=True)
+            w["B"][:, :w["k"]].copy_(hB[:, :w["k"]], non_blocking=True)
+            pkg.check(call(w))
+            hC.copy_(w["C"][:, :w["k"]], non_blocking=True)
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e_start.elapsed_time(e_end) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": round(world * step_bytes / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)}
+
+    # ---- CPU oracle baseline (rank 0, N = 1) --------------------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, desc, cores, _ = oracle_sample_run("f32", 1, 0)
+        cpu = {"value": round(v, 4), "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc}
+
+    n_launch = args.steps * sum(launches_per_call(w["op"], w["k"]) for w in work32)
+    line = {
+        "metric": "TSM2R/TSM2L achieved HBM GB/s (binary32 sweep)", "value": round(value, 2), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(mean_step_ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (device-generated splitmix64 uniform[-1,1))",
+        "config": {"workload": WORKLOAD, "l2": "flushed before every launch (memset of 2x L2)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "step_wall_s": round(wall / args.steps, 4)},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
+        "clocks": clock_rec, "fp64": fp64, "cases": case_rows, "src_hash": src_hash(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cublas", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,161 @@
+/*
+ * tsm2.h -- C ABI of the GB300 tall-and-skinny matrix-multiply library.
+ *
+ * Operation (Sec. 2.1 of Rivera et al., "TSM2X: High-Performance
+ * Tall-and-Skinny Matrix-Matrix Multiplication on GPUs"):
+ *
+ *     C(m x k) = A(m x n) * B(n x k),  C(i,c) = sum_j A(i,j) B(j,c)
+ *
+ * Naming: A is m x n, B is n x k, C is m x k, so n is the inner (reduced)
+ * dimension and k the skinny one.  (The paper calls the inner dimension k
+ * and the skinny one n.)
+ *
+ *  - TSM2R (Sec. 3.1, Algorithms 2-4): a large, roughly square A times a
+ *    tall-and-skinny B, m ~ n >> k.
+ *  - TSM2L (Sec. 3.2, Algorithm 5): a tall-and-skinny A times a small
+ *    square B, m >> n ~ k.
+ *
+ * Both entry points compute the same function; they differ in the kernel
+ * schedule they select, and TSM2L limits n and k.
+ *
+ * Common conventions for every matrix entry point below:
+ *  - Layout: column-major.  Element (i, j) of X is X[i + j * ldx].
+ *  - Pointers: DEVICE pointers to caller-owned memory on the current CUDA
+ *    device.  The library never frees or retains them.
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are asynchronous with respect to the host; results are ready once
+ *    the stream reaches the point of the call.
+ *  - Semantics: C is overwritten (beta = 0); its previous contents are never
+ *    read.  Rows m .. ldc-1 of C are never written.  C must not overlap A or
+ *    B (checked on address ranges: TSM2_ERR_INVALID_VALUE).
+ *  - Quick returns: m == 0 or k == 0 does nothing and returns SUCCESS;
+ *    n == 0 sets C to zero (the empty sum).
+ *  - Errors (checked before anything is launched; nothing is launched on
+ *    error):
+ *      TSM2_ERR_INVALID_VALUE  m, n or k negative; lda < max(1,m);
+ *                              ldb < max(1,n); ldc < max(1,m); a NULL
+ *                              pointer for a non-empty operand; overlap.
+ *      TSM2_ERR_UNSUPPORTED    see each entry point.
+ *      TSM2_ERR_CUDA           a CUDA runtime error at launch time; the
+ *                              message is in tsm2_get_last_error_string().
+ *    Faults during execution surface at the caller's next synchronisation,
+ *    as for any CUDA kernel.  A pipeline wait that exceeds its time bound
+ *    sets a device status word instead of hanging; tsm2_get_device_status()
+ *    reports it as TSM2_ERR_TIMEOUT.
+ *  - Alignment: any alignment is accepted.  16-byte aligned base pointers
+ *    with leading dimensions whose byte size is a multiple of 16 select the
+ *    bulk-copy (TMA) path; anything else selects a slower path that loads
+ *    element by element.  Both give results within the same error bound.
+ *  - Accuracy: every C(i,c) is a sum of the n products computed with fused
+ *    multiply-adds in the input precision; |C - AB| <= gamma_n |A||B|
+ *    componentwise, gamma_n = n u / (1 - n u).  The summation order is fixed
+ *    for a given (shape, device), so repeated calls are bitwise identical.
+ *  - Scratch: kernels that split the inner dimension over several thread
+ *    blocks combine partial sums through a per-(device, stream) workspace
+ *    that the library allocates lazily with cudaMalloc on first use and
+ *    grows when needed; tsm2_shutdown() frees it.  Two calls in flight at
+ *    once on the SAME stream are ordered by the stream and never race.
+ */
+#ifndef TSM2_H
+#define TSM2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tsm2_status {
+    TSM2_SUCCESS = 0,
+    TSM2_ERR_INVALID_VALUE = 1,
+    TSM2_ERR_UNSUPPORTED = 2,
+    TSM2_ERR_CUDA = 3,
+    TSM2_ERR_TIMEOUT = 4
+} tsm2_status;
+
+/* TSM2R, binary64.  A is streamed from device memory once per group of up
+ * to 16 columns of C (Sec. 3.1.2, outer-product form of Algorithm 2; the
+ * t2 loop of Algorithm 4 re-reads A ceil(k/16) times).  Any k >= 0. */
+tsm2_status tsm2r_d(int64_t m, int64_t n, int64_t k,
+                    const double *A, int64_t lda,
+                    const double *B, int64_t ldb,
+                    double *C, int64_t ldc, void *stream);
+
+/* TSM2R, binary32.  Same contract as tsm2r_d. */
+tsm2_status tsm2r_s(int64_t m, int64_t n, int64_t k,
+                    const float *A, int64_t lda,
+                    const float *B, int64_t ldb,
+                    float *C, int64_t ldc, void *stream);
+
+/* TSM2L, binary64 (Sec. 3.2, Algorithm 5: a persistent grid of thread
+ * blocks strides over row blocks of the tall-and-skinny A; B is held on
+ * chip).  TSM2_ERR_UNSUPPORTED if n > 64 or k > 64. */
+tsm2_status tsm2l_d(int64_t m, int64_t n, int64_t k,
+                    const double *A, int64_t lda,
+                    const double *B, int64_t ldb,
+                    double *C, int64_t ldc, void *stream);
+
+/* TSM2L, binary32.  Same contract as tsm2l_d. */
+tsm2_status tsm2l_s(int64_t m, int64_t n, int64_t k,
+                    const float *A, int64_t lda,
+                    const float *B, int64_t ldb,
+                    float *C, int64_t ldc, void *stream);
+
+/* Message describing the last error returned to the calling host thread
+ * (thread-local; valid until that thread's next call). Never NULL. */
+const char *tsm2_get_last_error_string(void);
+
+/* Synchronises `stream`, then reads and clears the current device's status
+ * word.  Returns TSM2_ERR_TIMEOUT if a kernel of this library gave up on a
+ * bounded pipeline wait since the previous call (its output is then
+ * undefined), TSM2_ERR_CUDA if synchronisation failed, else SUCCESS. */
+tsm2_status tsm2_get_device_status(void *stream);
+
+/* Frees every workspace the library allocated (all devices).  Call with no
+ * library work in flight.  The library stays usable; it reallocates lazily. */
+void tsm2_shutdown(void);
+
+/* ---- Tuning and debugging knobs (process-wide, not thread-safe) ---------- */
+
+/* Upper bound, in nanoseconds, of every pipeline wait inside the kernels
+ * (default 1e9).  0 means a single attempt, which forces the timeout path;
+ * used by tests of the error path. */
+void tsm2_set_wait_budget_ns(int64_t ns);
+
+/* Kernel path selection: 0 = automatic (default), 1 = always the
+ * element-wise path, 2 = the bulk-copy path when alignment allows. */
+void tsm2_set_path(int path);
+
+/* Number of thread blocks of the persistent grid (0 = automatic: one per
+ * SM, limited so each block gets at least a few work units). */
+void tsm2_set_grid(int blocks);
+
+/* Name of the kernel configuration the last call on this thread launched
+ * (for reports and tests). */
+const char *tsm2_last_config(void);
+
+/* ---- Synthetic inputs (definition in tsm2_inputs: splitmix64 counter
+ * stream per (seed, matrix_id); element (i,j) of the logical rows x cols
+ * matrix is draw i + j*rows).  Column-major, leading dimension ldx.  These
+ * exist so that multi-gigabyte benchmark inputs can be generated in device
+ * memory; they are not part of the multiply. ------------------------------ */
+tsm2_status tsm2_fill_uniform_d(int64_t rows, int64_t cols, uint64_t seed, uint64_t matrix_id,
+                                double *X, int64_t ldx, void *stream);
+tsm2_status tsm2_fill_uniform_s(int64_t rows, int64_t cols, uint64_t seed, uint64_t matrix_id,
+                                float *X, int64_t ldx, void *stream);
+tsm2_status tsm2_fill_int_small_d(int64_t rows, int64_t cols, uint64_t seed, uint64_t matrix_id,
+                                  double *X, int64_t ldx, void *stream);
+tsm2_status tsm2_fill_int_small_s(int64_t rows, int64_t cols, uint64_t seed, uint64_t matrix_id,
+                                  float *X, int64_t ldx, void *stream);
+tsm2_status tsm2_fill_normal_ih_d(int64_t rows, int64_t cols, uint64_t seed, uint64_t matrix_id,
+                                  double scale, double *X, int64_t ldx, void *stream);
+tsm2_status tsm2_fill_normal_ih_s(int64_t rows, int64_t cols, uint64_t seed, uint64_t matrix_id,
+                                  double scale, float *X, int64_t ldx, void *stream);
+tsm2_status tsm2_fill_logmag_s(int64_t rows, int64_t cols, uint64_t seed, uint64_t matrix_id,
+                               float *X, int64_t ldx, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSM2_H */

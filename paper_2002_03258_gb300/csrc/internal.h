@@ -1,0 +1,69 @@
+// Host-side declarations shared between the C ABI (tsm2_api.cu) and the
+// translation units that hold the kernels.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tsm2 {
+
+// One launch of a multiply kernel on a column chunk of at most KC columns of
+// C.  All pointers are device pointers; `k` is the number of live columns.
+struct GemmArgs {
+    int64_t m, n;
+    int k;
+    const void *A;
+    int64_t lda;
+    const void *B;
+    int64_t ldb;
+    void *C;
+    int64_t ldc;
+};
+
+// Everything a stream (TMA) kernel launch needs besides the operands.
+struct StreamLaunch {
+    GemmArgs g;
+    CUtensorMap mapA;   // A: dims {m, n}, box {BOXM, BNS}
+    CUtensorMap mapB;   // B: dims {n, k}, box {BNS, KC} (unused when B is resident)
+    void *ws;           // partial-sum slots, 256-byte aligned
+    int *counters;      // one arrival counter per row block, zero between launches
+    unsigned *status;   // device status word
+    int64_t wait_ns;    // bound of every pipeline wait
+    int grid;           // thread blocks of the persistent grid
+    bool c_vec;         // C base and ldc allow 16-byte stores
+};
+
+// Static description of a compiled stream-kernel configuration.
+struct StreamShape {
+    const char *name;
+    int elem;        // bytes per element
+    int KC;          // C columns per pass
+    int BM;          // rows per row block
+    int BNS;         // inner-dimension columns per pipeline stage
+    int BOXM;        // rows per TMA box
+    int gran_rows;   // 1: split inner dim at stage granularity; 0: whole row blocks
+    bool b_resident; // B loaded once into shared memory (requires n <= n_max_resident)
+    int n_max_resident;
+    int smem_bytes;
+    int threads;
+};
+
+// Kernel selectors: op 'r' (TSM2R schedule) or 'l' (TSM2L schedule).
+// Returns nullptr if no compiled configuration covers (elem, op, kc).
+const StreamShape *stream_shape(int elem, char op, int kc);
+cudaError_t stream_launch(const StreamShape *shape, const StreamLaunch &L, cudaStream_t stream);
+
+// Element-wise fallback (any alignment), Algorithm 3 style.
+cudaError_t simple_launch(int elem, const GemmArgs &g, unsigned *status, cudaStream_t stream);
+int simple_kc_max();
+
+// Work partition of the persistent grid (shared by host sizing and kernels).
+struct Partition {
+    int64_t num_rb;  // row blocks
+    int64_t upr;     // stages (units) per row block
+    int64_t gran;    // units per indivisible group
+    int64_t ngroups; // total groups
+};
+
+}  // namespace tsm2

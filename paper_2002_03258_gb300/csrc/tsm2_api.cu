@@ -1,0 +1,356 @@
+// C ABI of the library (declared in include/tsm2.h): argument checking,
+// choice of kernel path and configuration, tensor-map encoding, workspace
+// management and the device status word.
+#include "internal.h"
+#include "tsm2.h"
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+
+namespace tsm2 {
+namespace {
+
+__device__ unsigned int g_status_word;  // per device; bit kStatusTimeout set by kernels
+
+thread_local std::string t_last_error = "no error";
+thread_local const char *t_last_config = "none";
+
+int64_t g_wait_ns = 1000000000LL;
+int g_path = 0;
+int g_grid_override = 0;
+
+tsm2_status set_error(tsm2_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+    return s;
+}
+
+tsm2_status cuda_error(cudaError_t e, const char *what) {
+    return set_error(TSM2_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// ---- per-device state ------------------------------------------------------
+
+struct DeviceState {
+    bool init = false;
+    int sm_count = 0;
+    unsigned *status = nullptr;  // device address of g_status_word
+};
+
+std::mutex g_mu;
+DeviceState g_dev[64];
+
+struct Workspace {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    size_t counter_bytes = 0;
+};
+std::map<std::pair<int, uintptr_t>, Workspace> g_ws;  // (device, stream) -> workspace
+
+tsm2_status device_state(DeviceState **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return set_error(TSM2_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState &d = g_dev[dev];
+    if (!d.init) {
+        e = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_error(e, "cudaDeviceGetAttribute");
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_status_word);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(status)");
+        d.status = static_cast<unsigned *>(p);
+        d.init = true;
+    }
+    *out = &d;
+    return TSM2_SUCCESS;
+}
+
+// Returns a workspace of at least `bytes` (256-byte aligned) whose first
+// `counter_bytes` bytes are zero.  The counters return to zero after every
+// completed launch, so they are only cleared when (re)allocated.
+tsm2_status workspace(cudaStream_t stream, size_t counter_bytes, size_t slot_bytes, void **ws, int **counters) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    counter_bytes = (counter_bytes + 255) / 256 * 256;
+    std::lock_guard<std::mutex> lk(g_mu);
+    Workspace &w = g_ws[{dev, reinterpret_cast<uintptr_t>(stream)}];
+    if (!w.ptr || w.counter_bytes < counter_bytes || w.bytes < w.counter_bytes + slot_bytes) {
+        const size_t cb = std::max(counter_bytes, w.counter_bytes);
+        const size_t nb = std::max((cb + slot_bytes) * 5 / 4 + 4096, w.bytes);
+        if (w.ptr) {
+            // Pending work of this stream may still use the old buffer.
+            e = cudaStreamSynchronize(stream);
+            if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize(workspace)");
+            cudaFree(w.ptr);
+            w = Workspace{};
+        }
+        void *p = nullptr;
+        e = cudaMalloc(&p, nb);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(workspace)");
+        e = cudaMemsetAsync(p, 0, cb, stream);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(workspace counters)");
+        w.ptr = p;
+        w.bytes = nb;
+        w.counter_bytes = cb;
+    }
+    *counters = static_cast<int *>(w.ptr);
+    *ws = static_cast<char *>(w.ptr) + w.counter_bytes;
+    return TSM2_SUCCESS;
+}
+
+// ---- tensor maps -----------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+tsm2_status encode_2d(CUtensorMap *map, int elem, const void *base, int64_t rows, int64_t cols, int64_t ld,
+                      int box_rows, int box_cols) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return set_error(TSM2_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
+    const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * elem)};
+    const cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(map, elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                          const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(TSM2_ERR_CUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+    return TSM2_SUCCESS;
+}
+
+// ---- argument checks ---------------------------------------------------------
+
+bool ranges_overlap(const void *a, size_t abytes, const void *b, size_t bbytes) {
+    if (!a || !b || !abytes || !bbytes) return false;
+    const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+    return a0 < b0 + bbytes && b0 < a0 + abytes;
+}
+
+size_t span_bytes(int64_t rows, int64_t cols, int64_t ld, int elem) {
+    if (rows <= 0 || cols <= 0) return 0;
+    return (size_t)(((cols - 1) * ld + rows) * elem);
+}
+
+tsm2_status check_args(const char *fn, int64_t m, int64_t n, int64_t k, const void *A, int64_t lda, const void *B,
+                       int64_t ldb, const void *C, int64_t ldc, int elem) {
+    if (m < 0 || n < 0 || k < 0)
+        return set_error(TSM2_ERR_INVALID_VALUE, "%s: negative dimension (m=%lld n=%lld k=%lld)", fn, (long long)m,
+                         (long long)n, (long long)k);
+    if (lda < (m > 1 ? m : 1)) return set_error(TSM2_ERR_INVALID_VALUE, "%s: lda=%lld < max(1,m)", fn, (long long)lda);
+    if (ldb < (n > 1 ? n : 1)) return set_error(TSM2_ERR_INVALID_VALUE, "%s: ldb=%lld < max(1,n)", fn, (long long)ldb);
+    if (ldc < (m > 1 ? m : 1)) return set_error(TSM2_ERR_INVALID_VALUE, "%s: ldc=%lld < max(1,m)", fn, (long long)ldc);
+    if (m > 0 && k > 0 && C == nullptr) return set_error(TSM2_ERR_INVALID_VALUE, "%s: C is NULL", fn);
+    if (m > 0 && n > 0 && k > 0 && A == nullptr) return set_error(TSM2_ERR_INVALID_VALUE, "%s: A is NULL", fn);
+    if (m > 0 && n > 0 && k > 0 && B == nullptr) return set_error(TSM2_ERR_INVALID_VALUE, "%s: B is NULL", fn);
+    if (m > 0 && k > 0) {
+        const size_t cb = span_bytes(m, k, ldc, elem);
+        if ((n > 0 && ranges_overlap(C, cb, A, span_bytes(m, n, lda, elem))) ||
+            (n > 0 && ranges_overlap(C, cb, B, span_bytes(n, k, ldb, elem))))
+            return set_error(TSM2_ERR_INVALID_VALUE, "%s: C overlaps A or B", fn);
+    }
+    return TSM2_SUCCESS;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// ---- the multiply ------------------------------------------------------------
+
+tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_t k, const void *A, int64_t lda,
+                 const void *B, int64_t ldb, void *C, int64_t ldc, void *stream_v) {
+    tsm2_status st = check_args(fn, m, n, k, A, lda, B, ldb, C, ldc, elem);
+    if (st != TSM2_SUCCESS) return st;
+    if (op == 'l' && (n > 64 || k > 64))
+        return set_error(TSM2_ERR_UNSUPPORTED, "%s: TSM2L needs n <= 64 and k <= 64 (got n=%lld k=%lld)", fn,
+                         (long long)n, (long long)k);
+    if (m == 0 || k == 0) {
+        t_last_config = "empty";
+        return TSM2_SUCCESS;
+    }
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    if (n == 0) {
+        t_last_config = "zero-fill";
+        cudaError_t e = cudaMemset2DAsync(C, (size_t)ldc * elem, 0, (size_t)m * elem, (size_t)k, stream);
+        return e == cudaSuccess ? TSM2_SUCCESS : cuda_error(e, "cudaMemset2DAsync");
+    }
+    DeviceState *dev = nullptr;
+    st = device_state(&dev);
+    if (st != TSM2_SUCCESS) return st;
+
+    // The bulk-copy path needs 16-byte aligned bases and row strides, and
+    // 32-bit tensor coordinates.  The TSM2L schedule reads B with ordinary
+    // loads, so only A matters there.
+    const bool a_ok = aligned16(A) && ((lda * elem) % 16 == 0) && m < (1ll << 31) - 4096 && n < (1ll << 31);
+    const bool b_ok = op == 'l' || (aligned16(B) && ((ldb * elem) % 16 == 0));
+    const bool use_stream = g_path != 1 && a_ok && b_ok;
+
+    const int kc_max = use_stream ? (op == 'l' ? 32 : 16) : simple_kc_max();
+    for (int64_t c0 = 0; c0 < k; c0 += kc_max) {
+        GemmArgs g;
+        g.m = m;
+        g.n = n;
+        g.k = (int)((k - c0) < kc_max ? (k - c0) : kc_max);
+        g.A = A;
+        g.lda = lda;
+        g.B = static_cast<const char *>(B) + (size_t)c0 * ldb * elem;
+        g.ldb = ldb;
+        g.C = static_cast<char *>(C) + (size_t)c0 * ldc * elem;
+        g.ldc = ldc;
+        cudaError_t e;
+        if (!use_stream) {
+            t_last_config = elem == 8 ? "simple_f64" : "simple_f32";
+            e = simple_launch(elem, g, dev->status, stream);
+            if (e != cudaSuccess) return cuda_error(e, "simple kernel launch");
+            continue;
+        }
+        int kc = 2;
+        while (kc < g.k) kc *= 2;
+        const StreamShape *shape = stream_shape(elem, op, kc);
+        if (!shape) return set_error(TSM2_ERR_UNSUPPORTED, "%s: no kernel configuration for k chunk %d", fn, g.k);
+        StreamLaunch L;
+        std::memset(&L, 0, sizeof L);
+        L.g = g;
+        st = encode_2d(&L.mapA, elem, A, m, n, lda, shape->BOXM, shape->BNS);
+        if (st != TSM2_SUCCESS) return st;
+        if (!shape->b_resident) {
+            st = encode_2d(&L.mapB, elem, g.B, n, g.k, ldb, shape->BNS, shape->KC);
+            if (st != TSM2_SUCCESS) return st;
+        }
+        const int64_t num_rb = (m + shape->BM - 1) / shape->BM;
+        const int64_t upr = (n + shape->BNS - 1) / shape->BNS;
+        const int64_t ngroups = shape->b_resident ? num_rb : num_rb * upr;
+        int64_t grid = dev->sm_count;
+        if (!shape->b_resident) {
+            // At least four stages per block so partial sums stay a small
+            // fraction of the traffic.
+            const int64_t cap = (num_rb * upr) / 4;
+            if (cap < grid) grid = cap;
+        }
+        if (grid > ngroups) grid = ngroups;
+        if (g_grid_override > 0) grid = g_grid_override < ngroups ? g_grid_override : ngroups;
+        if (grid < 1) grid = 1;
+        L.grid = (int)grid;
+        void *ws = nullptr;
+        int *counters = nullptr;
+        if (!shape->b_resident) {
+            const size_t slots = (size_t)(grid + num_rb) * shape->KC * shape->BM * elem;
+            st = workspace(stream, (size_t)num_rb * sizeof(int), slots, &ws, &counters);
+            if (st != TSM2_SUCCESS) return st;
+        }
+        L.ws = ws;
+        L.counters = counters;
+        L.status = dev->status;
+        L.wait_ns = g_wait_ns;
+        L.c_vec = aligned16(g.C) && ((ldc * elem) % 16 == 0);
+        t_last_config = shape->name;
+        e = stream_launch(shape, L, stream);
+        if (e != cudaSuccess) return cuda_error(e, "stream kernel launch");
+    }
+    return TSM2_SUCCESS;
+}
+
+}  // namespace
+}  // namespace tsm2
+
+using namespace tsm2;
+
+extern "C" {
+
+tsm2_status tsm2r_d(int64_t m, int64_t n, int64_t k, const double *A, int64_t lda, const double *B, int64_t ldb,
+                    double *C, int64_t ldc, void *stream) {
+    return gemm("tsm2r_d", 'r', 8, m, n, k, A, lda, B, ldb, C, ldc, stream);
+}
+
+tsm2_status tsm2r_s(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb,
+                    float *C, int64_t ldc, void *stream) {
+    return gemm("tsm2r_s", 'r', 4, m, n, k, A, lda, B, ldb, C, ldc, stream);
+}
+
+tsm2_status tsm2l_d(int64_t m, int64_t n, int64_t k, const double *A, int64_t lda, const double *B, int64_t ldb,
+                    double *C, int64_t ldc, void *stream) {
+    return gemm("tsm2l_d", 'l', 8, m, n, k, A, lda, B, ldb, C, ldc, stream);
+}
+
+tsm2_status tsm2l_s(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb,
+                    float *C, int64_t ldc, void *stream) {
+    return gemm("tsm2l_s", 'l', 4, m, n, k, A, lda, B, ldb, C, ldc, stream);
+}
+
+const char *tsm2_get_last_error_string(void) { return t_last_error.c_str(); }
+
+const char *tsm2_last_config(void) { return t_last_config; }
+
+tsm2_status tsm2_get_device_status(void *stream) {
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+    unsigned w = 0;
+    e = cudaMemcpyFromSymbol(&w, g_status_word, sizeof w);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyFromSymbol(status)");
+    if (w == 0) return TSM2_SUCCESS;
+    const unsigned zero = 0;
+    e = cudaMemcpyToSymbol(g_status_word, &zero, sizeof zero);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyToSymbol(status)");
+    // An abandoned launch may leave arrival counters non-zero: clear them all
+    // on this device.
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        for (auto &kv : g_ws)
+            if (kv.first.first == dev && kv.second.ptr) cudaMemset(kv.second.ptr, 0, kv.second.counter_bytes);
+    }
+    cudaDeviceSynchronize();
+    return set_error(TSM2_ERR_TIMEOUT, "a pipeline wait exceeded its bound; the output of that call is undefined");
+}
+
+void tsm2_shutdown(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &kv : g_ws) {
+        if (!kv.second.ptr) continue;
+        cudaSetDevice(kv.first.first);
+        cudaFree(kv.second.ptr);
+    }
+    g_ws.clear();
+    cudaSetDevice(cur);
+}
+
+void tsm2_set_wait_budget_ns(int64_t ns) { g_wait_ns = ns < 0 ? 0 : ns; }
+
+void tsm2_set_path(int path) { g_path = path; }
+
+void tsm2_set_grid(int blocks) { g_grid_override = blocks < 0 ? 0 : blocks; }
+
+}  // extern "C"

@@ -1,0 +1,544 @@
+// Bulk-copy (TMA) path for TSM2R and TSM2L on sm_103a.
+//
+// What it computes: C(m x k) = A(m x n) B(n x k), column-major, for up to KC
+// columns of C per launch (the host loops over column chunks, which is the
+// t2 loop of Algorithm 4, Sec. 3.1.4).
+//
+// How it maps the paper's design onto GB300:
+//  * Outer product, A read once (Algorithm 2, Sec. 3.1.2): every lane owns R
+//    rows of C and keeps all KC accumulators of each row in registers; every
+//    element of A that reaches the lane is multiplied into all KC of them.
+//  * B staged on chip and read by broadcast (Algorithm 3, Sec. 3.1.3-3.1.4):
+//    the rows of B that pair with the current A tile sit in shared memory in
+//    column order; all lanes of a warp read the same 16 bytes at once.
+//  * Prefetching (Algorithm 4, Sec. 3.1.5) becomes a STAGES-deep ring of
+//    shared-memory buffers filled by the tensor-memory accelerator: one
+//    producer lane issues 2-D bulk tensor copies of A tiles (BM rows x BNS
+//    columns) STAGES-1 tiles ahead of the consumer warps, signalling
+//    completion on per-stage mbarriers; consumers release a stage through a
+//    second mbarrier.  The bytes in flight per SM are set by Little's law
+//    (Sec. 3.1.8) rather than by registers per thread.
+//  * Fewer, longer-lived threads (Algorithm 5, Sec. 3.2.2): the grid is
+//    persistent, one thread block per SM.  The work units (one pipeline
+//    stage each, i.e. a BM x BNS tile of A) are numbered row block by row
+//    block and every block takes a contiguous run of them, so all blocks get
+//    the same amount of work whatever the shape.
+//  * When a block's run starts or ends inside a row block (TSM2R schedule),
+//    its partial sums go to a workspace slot; the last block to finish a row
+//    block (an atomic arrival counter, no waiting) adds the slots in a fixed
+//    order and writes C.  Results are therefore bitwise reproducible.
+//  * TSM2R schedule: the 8 consumer warps of a block share the rows of one
+//    row block and split the inner-dimension columns of every stage; their
+//    partial sums meet once per row block in shared memory (fixed warp
+//    order).  TSM2L schedule: the warps split the rows (BM = 8 x 32 x R),
+//    the whole of B (n <= 64) is loaded once per block, and runs are aligned
+//    to row blocks, so no partial sums are ever needed.
+//
+// Every wait is bounded (mbar_wait_bounded); on timeout the block records it
+// in the status word, stops consuming, lets its in-flight copies land and
+// exits normally.
+#include "common.cuh"
+#include "internal.h"
+
+#include <mutex>
+
+namespace tsm2 {
+
+namespace {
+
+constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+constexpr int cmin(int a, int b) { return a < b ? a : b; }
+
+template <typename T_, int KC_, int NV_, int WR_, int WC_, int JW_, int STAGES_, bool BRES_, int NRES_>
+struct Cfg {
+    using T = T_;
+    using VT = Vec16<T>;
+    using vec_t = typename VT::type;
+    static constexpr int V = VT::n;          // elements per 16-byte vector
+    static constexpr int KC = KC_;           // C columns per pass
+    static constexpr int NV = NV_;           // 16-byte row vectors per lane
+    static constexpr int WR = WR_;           // warps along rows
+    static constexpr int WC = WC_;           // warps along the inner dimension
+    static constexpr int JW = JW_;           // inner columns per warp per stage
+    static constexpr int STAGES = STAGES_;
+    static constexpr bool BRES = BRES_;      // B resident in shared memory
+    static constexpr int NRES = NRES_;       // inner extent reserved for resident B
+    static constexpr int R = NV * V;         // rows per lane
+    static constexpr int BM = WR * 32 * R;   // rows per row block
+    static constexpr int BNS = WC * JW;      // inner columns per stage
+    static constexpr int NW = WR * WC;       // consumer warps
+    static constexpr int NT = NW * 32;       // consumer threads
+    static constexpr int THREADS = NT + 128; // plus one producer warpgroup (one lane works)
+    static_assert(NW == 8, "register split below assumes 2 consumer warpgroups");
+    static constexpr int BOXM = BM < 256 ? BM : 256;
+    static constexpr int NBOX = BM / BOXM;
+    static constexpr int JV = V;             // inner columns per B vector
+    static constexpr int CC = cmin(KC, 4);   // C columns per cross-warp reduction round
+    static constexpr int A_STAGE = BM * BNS;                 // elements
+    static constexpr int B_STAGE = BRES ? 0 : BNS * KC;      // elements
+    static constexpr int RED = WC > 1 ? WC * CC * BM : 0;    // elements
+    static constexpr int BRES_ELEMS = BRES ? KC * NRES : 0;  // elements
+    static constexpr uint32_t TX_BYTES = (uint32_t)((A_STAGE + B_STAGE) * sizeof(T));
+    static constexpr size_t OFF_A = 0;
+    static constexpr size_t OFF_B = OFF_A + (size_t)STAGES * A_STAGE * sizeof(T);
+    static constexpr size_t OFF_BRES = OFF_B + (size_t)STAGES * B_STAGE * sizeof(T);
+    static constexpr size_t OFF_RED = OFF_BRES + (size_t)BRES_ELEMS * sizeof(T);
+    static constexpr size_t OFF_BAR = align_up(OFF_RED + (size_t)RED * sizeof(T), 16);
+    static constexpr size_t OFF_FLAGS = OFF_BAR + 2 * STAGES * sizeof(uint64_t);
+    static constexpr size_t SMEM = OFF_FLAGS + 16 + 128;  // + slack for 128-byte alignment
+
+    static_assert(JW % JV == 0, "a warp's columns must be whole B vectors");
+    static_assert((BNS * sizeof(T)) % 16 == 0, "TMA inner box extent must be 16-byte multiple");
+    static_assert((A_STAGE * sizeof(T)) % 128 == 0, "stage buffers stay 128-byte aligned");
+    static_assert((B_STAGE * sizeof(T)) % 128 == 0 || BRES, "stage buffers stay 128-byte aligned");
+    static_assert(BM % BOXM == 0 && (32 * V) <= BOXM, "a warp's vector row group fits one box");
+    static_assert(WC == 1 || (CC * BM) % NT == 0, "reduction rounds split evenly over threads");
+    static_assert(!BRES || NRES % BNS == 0, "resident B covers whole stages");
+    static_assert(SMEM <= 227 * 1024, "shared memory per block");
+};
+
+struct Params {
+    int64_t m, n;
+    int k;
+    const void *B;  // raw B for the resident copy
+    int64_t ldb;
+    void *C;
+    int64_t ldc;
+    void *ws;
+    int *counters;
+    unsigned *status;
+    int64_t wait_ns;
+    int64_t upr;      // units (stages) per row block
+    int64_t gran;     // units per indivisible group
+    int64_t ngroups;  // groups in total
+    int c_vec;
+};
+
+// Block index that owns group x under the partition gs(g) = floor(g*NG/G).
+__device__ __forceinline__ int64_t owner_of(int64_t x, int64_t G, int64_t NG) {
+    return ((x + 1) * G + NG - 1) / NG - 1;
+}
+
+// Register split (setmaxnreg): launched with 384 threads x 168 registers =
+// 64512; the producer warpgroup drops to 40 and the two consumer warpgroups
+// rise to 232: 4*32*40 + 8*32*232 = 64512, exactly the launch pool, and every
+// SM sub-partition (one producer warp + two consumer warps) holds
+// 32*(40 + 2*232) = 16128 <= 16384 registers.
+constexpr int kProducerRegs = 40;
+constexpr int kConsumerRegs = 232;
+static_assert(4 * 32 * kProducerRegs + 8 * 32 * kConsumerRegs <= 384 * 168, "register split exceeds launch pool");
+
+template <class K>
+__global__ void __launch_bounds__(384, 1)
+stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const Params p) {
+    using T = typename K::T;
+    using vec_t = typename K::vec_t;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(align_up(reinterpret_cast<uintptr_t>(smem_raw), 128));
+    T *sA = reinterpret_cast<T *>(smem + K::OFF_A);
+    T *sB = reinterpret_cast<T *>(smem + K::OFF_B);
+    T *sBres = reinterpret_cast<T *>(smem + K::OFF_BRES);
+    T *sRed = reinterpret_cast<T *>(smem + K::OFF_RED);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + K::OFF_BAR);
+    uint64_t *empty = full + K::STAGES;
+    volatile int *flags = reinterpret_cast<volatile int *>(smem + K::OFF_FLAGS);  // [0] abort, [1] last
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t G = gridDim.x;
+    const int64_t g = blockIdx.x;
+    const int64_t gs = g * p.ngroups / G;
+    const int64_t ge = (g + 1) * p.ngroups / G;
+    const int64_t u_begin = gs * p.gran;
+    const int64_t u_end = ge * p.gran;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < K::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], K::NW);
+        }
+        flags[0] = 0;
+        flags[1] = 0;
+        fence_mbar_init();
+    }
+    if constexpr (K::BRES) {
+        // Whole of B (n <= NRES) once per block, column c at sBres[c*NRES + j],
+        // zero beyond n and k so padded lanes contribute exact zeros.
+        const T *B = static_cast<const T *>(p.B);
+        for (int t = threadIdx.x; t < K::KC * K::NRES; t += K::THREADS) {
+            const int j = t % K::NRES;
+            const int c = t / K::NRES;
+            sBres[t] = (j < p.n && c < p.k) ? B[j + (int64_t)c * p.ldb] : T(0);
+        }
+    }
+    __syncthreads();
+
+    if (warp < 4) {
+        // ---------------- producer warpgroup: one lane issues all bulk copies ----------------
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProducerRegs));
+        if (warp == 0 && lane == 0) {
+            prefetch_tensormap(&mapA);
+            if constexpr (!K::BRES) prefetch_tensormap(&mapB);
+            const uint64_t policy = l2_policy_evict_first();
+            int s = 0;
+            uint32_t ph = 0;
+            uint32_t issued = 0, last_par = 0;  // per-stage: issued at least once, parity of last issue
+            int64_t rb = u_begin / p.upr;
+            int64_t jc = u_begin - rb * p.upr;
+            for (int64_t u = u_begin; u < u_end; ++u) {
+                if (flags[0]) break;
+                if (!mbar_wait_bounded(&empty[s], ph ^ 1u, p.wait_ns, flags)) {
+                    flags[0] = 1;
+                    atomicOr(p.status, kStatusTimeout);
+                    break;
+                }
+                mbar_arrive_expect_tx(&full[s], K::TX_BYTES);
+                T *dstA = sA + (size_t)s * K::A_STAGE;
+                const int32_t x0 = (int32_t)(rb * K::BM);
+                const int32_t y0 = (int32_t)(jc * K::BNS);
+#pragma unroll
+                for (int q = 0; q < K::NBOX; ++q)
+                    tma_load_2d_hint(dstA + q * K::BOXM * K::BNS, &mapA, x0 + q * K::BOXM, y0, &full[s], policy);
+                if constexpr (!K::BRES) tma_load_2d(sB + (size_t)s * K::B_STAGE, &mapB, y0, 0, &full[s]);
+                issued |= 1u << s;
+                last_par = (last_par & ~(1u << s)) | (ph << s);
+                if (++s == K::STAGES) { s = 0; ph ^= 1u; }
+                if (++jc == p.upr) { jc = 0; ++rb; }
+            }
+            // Let every copy this block started land before the block can exit.
+            for (int t = 0; t < K::STAGES; ++t)
+                if (issued & (1u << t)) (void)mbar_wait_bounded(&full[t], (last_par >> t) & 1u, 4000000000LL, nullptr);
+        }
+        return;
+    }
+
+    // ---------------- consumers ----------------
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
+    const int cwarp = warp - 4;    // consumer warp 0 .. NW-1
+    const int wr = cwarp / K::WC;  // row group
+    const int wc = cwarp % K::WC;  // inner-column group
+    T acc[K::R][K::KC];
+#pragma unroll
+    for (int r = 0; r < K::R; ++r)
+#pragma unroll
+        for (int c = 0; c < K::KC; ++c) acc[r][c] = T(0);
+
+    // Rows of the row block owned by this lane: vector v covers rows
+    // row_of(v) .. row_of(v) + V - 1.
+    auto row_of = [&](int v) { return wr * 32 * K::R + v * 32 * K::V + lane * K::V; };
+
+    int s = 0;
+    uint32_t ph = 0;
+    bool aborted = false;
+    int64_t rb = u_begin / p.upr;
+    int64_t jc = u_begin - rb * p.upr;
+    int64_t piece_u0 = u_begin;
+
+    for (int64_t u = u_begin; u < u_end; ++u) {
+        if (!aborted) {
+            // Warp-uniform decision: the warp consumes the stage only if every
+            // lane saw it complete.
+            bool ok = !flags[0] && mbar_wait_bounded(&full[s], ph, p.wait_ns, flags);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                aborted = true;
+                if (lane == 0) {
+                    flags[0] = 1;
+                    atomicOr(p.status, kStatusTimeout);
+                }
+            }
+        }
+        if (!aborted) {
+            const T *a_st = sA + (size_t)s * K::A_STAGE;
+            const T *b_st;
+            int bstride;
+            if constexpr (K::BRES) {
+                b_st = sBres + jc * K::BNS;
+                bstride = K::NRES;
+            } else {
+                b_st = sB + (size_t)s * K::B_STAGE;
+                bstride = K::BNS;
+            }
+#pragma unroll
+            for (int jj = 0; jj < K::JW; jj += K::JV) {
+                const int j = wc * K::JW + jj;  // stage-local inner column of the first vector lane
+                T a[K::JV][K::R];
+#pragma unroll
+                for (int jv = 0; jv < K::JV; ++jv)
+#pragma unroll
+                    for (int v = 0; v < K::NV; ++v) {
+                        const int r = row_of(v);
+                        const int q = r / K::BOXM;
+                        const int rr = r - q * K::BOXM;
+                        const vec_t x =
+                            *reinterpret_cast<const vec_t *>(a_st + q * K::BOXM * K::BNS + (j + jv) * K::BOXM + rr);
+#pragma unroll
+                        for (int e = 0; e < K::V; ++e) a[jv][v * K::V + e] = K::VT::get(x, e);
+                    }
+#pragma unroll
+                for (int c = 0; c < K::KC; ++c) {
+                    const vec_t bv = *reinterpret_cast<const vec_t *>(b_st + c * bstride + j);
+#pragma unroll
+                    for (int jv = 0; jv < K::JV; ++jv) {
+                        const T b = K::VT::get(bv, jv);
+#pragma unroll
+                        for (int r = 0; r < K::R; ++r) acc[r][c] = fma(a[jv][r], b, acc[r][c]);
+                    }
+                }
+            }
+        }
+        // Release the stage to the producer.  A warp that gave up releases
+        // nothing more: the producer then stops too, so no copy is ever issued
+        // into a buffer whose previous copy may still be landing.
+        if (!aborted) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+        if (++s == K::STAGES) { s = 0; ph ^= 1u; }
+
+        const bool rb_end = (jc == p.upr - 1);
+        if (rb_end || u == u_end - 1) {
+            // ---------------- epilogue of one piece of row block rb ----------------
+            const int64_t rb_u0 = rb * p.upr;
+            const bool whole = (piece_u0 == rb_u0) && rb_end;
+            const int64_t row0 = rb * K::BM;
+            T *C = static_cast<T *>(p.C);
+            T *ws = static_cast<T *>(p.ws);
+            const int64_t NG = p.ngroups;
+            const int64_t gA = owner_of(rb_u0 / p.gran, G, NG);
+            const int64_t gB = owner_of((rb_u0 + p.upr - 1) / p.gran, G, NG);
+            const int64_t my_slot = g + rb;
+            const int tid = threadIdx.x - 128;  // 0 .. NT-1 for consumers
+
+            if constexpr (K::WC == 1) {
+                if (whole) {
+                    if (!aborted) {
+#pragma unroll
+                        for (int v = 0; v < K::NV; ++v) {
+                            const int64_t r0 = row0 + row_of(v);
+#pragma unroll
+                            for (int c = 0; c < K::KC; ++c) {
+                                if (c >= p.k) continue;
+                                T *dst = C + r0 + (int64_t)c * p.ldc;
+                                if (p.c_vec && r0 + K::V <= p.m) {
+                                    T tmp[K::V];
+#pragma unroll
+                                    for (int e = 0; e < K::V; ++e) tmp[e] = acc[v * K::V + e][c];
+                                    *reinterpret_cast<vec_t *>(dst) = K::VT::make(tmp);
+                                } else {
+#pragma unroll
+                                    for (int e = 0; e < K::V; ++e)
+                                        if (r0 + e < p.m) dst[e] = acc[v * K::V + e][c];
+                                }
+                            }
+                        }
+                    }
+                } else {
+                    // Partial sums in registers -> slot [KC][BM] at this lane's rows.
+                    T *slot = ws + my_slot * (int64_t)(K::KC * K::BM);
+#pragma unroll
+                    for (int v = 0; v < K::NV; ++v)
+#pragma unroll
+                        for (int c = 0; c < K::KC; ++c) {
+                            T tmp[K::V];
+#pragma unroll
+                            for (int e = 0; e < K::V; ++e) tmp[e] = acc[v * K::V + e][c];
+                            __stcg(reinterpret_cast<vec_t *>(slot + c * K::BM + row_of(v)), K::VT::make(tmp));
+                        }
+                }
+            } else {
+                // Cross-warp reduction in shared memory, CC columns per round,
+                // fixed order wc = 0 .. WC-1; output in the canonical layout
+                // e = c * BM + row, element e handled by consumer thread e % NT.
+                T *slot = ws + my_slot * (int64_t)(K::KC * K::BM);
+#pragma unroll
+                for (int c0 = 0; c0 < K::KC; c0 += K::CC) {
+                    named_bar_sync(1, K::NT);
+#pragma unroll
+                    for (int cc = 0; cc < K::CC; ++cc)
+#pragma unroll
+                        for (int v = 0; v < K::NV; ++v) {
+                            T tmp[K::V];
+#pragma unroll
+                            for (int e = 0; e < K::V; ++e) tmp[e] = acc[v * K::V + e][c0 + cc];
+                            *reinterpret_cast<vec_t *>(sRed + (wc * K::CC + cc) * K::BM + row_of(v)) = K::VT::make(tmp);
+                        }
+                    named_bar_sync(1, K::NT);
+#pragma unroll
+                    for (int q = 0; q < (K::CC * K::BM) / K::NT; ++q) {
+                        const int e = tid + q * K::NT;
+                        const int cc = e / K::BM;
+                        const int row = e - cc * K::BM;
+                        T sum = sRed[cc * K::BM + row];
+#pragma unroll
+                        for (int w2 = 1; w2 < K::WC; ++w2) sum += sRed[(w2 * K::CC + cc) * K::BM + row];
+                        const int c = c0 + cc;
+                        if (whole) {
+                            if (!aborted && c < p.k && row0 + row < p.m) C[row0 + row + (int64_t)c * p.ldc] = sum;
+                        } else {
+                            __stcg(slot + c * K::BM + row, sum);
+                        }
+                    }
+                }
+            }
+
+            if (!whole) {
+                // Publish this piece; the last arriving block of the row block
+                // adds all pieces in block order and writes C.
+                __threadfence();
+                named_bar_sync(1, K::NT);
+                if (tid == 0) {
+                    int last = 0;
+                    if (!flags[0]) {
+                        const int npieces = (int)(gB - gA + 1);
+                        const int old = atomicAdd(&p.counters[rb], 1);
+                        last = (old == npieces - 1);
+                        if (last) p.counters[rb] = 0;  // ready for the next launch
+                    }
+                    flags[1] = last;
+                }
+                named_bar_sync(1, K::NT);
+                if (flags[1]) {
+                    __threadfence();
+                    if constexpr (K::WC == 1) {
+#pragma unroll
+                        for (int v = 0; v < K::NV; ++v)
+#pragma unroll
+                            for (int c = 0; c < K::KC; ++c) {
+                                T sum[K::V];
+                                for (int64_t gp = gA; gp <= gB; ++gp) {
+                                    const vec_t x = __ldcg(reinterpret_cast<const vec_t *>(
+                                        ws + (gp + rb) * (int64_t)(K::KC * K::BM) + c * K::BM + row_of(v)));
+#pragma unroll
+                                    for (int e = 0; e < K::V; ++e)
+                                        sum[e] = (gp == gA) ? K::VT::get(x, e) : sum[e] + K::VT::get(x, e);
+                                }
+                                const int64_t r0 = row0 + row_of(v);
+                                if (c < p.k)
+#pragma unroll
+                                    for (int e = 0; e < K::V; ++e)
+                                        if (r0 + e < p.m) C[r0 + e + (int64_t)c * p.ldc] = sum[e];
+                            }
+                    } else {
+                        for (int e = tid; e < K::KC * K::BM; e += K::NT) {
+                            const int c = e / K::BM;
+                            const int row = e - c * K::BM;
+                            T sum = __ldcg(ws + (gA + rb) * (int64_t)(K::KC * K::BM) + e);
+                            for (int64_t gp = gA + 1; gp <= gB; ++gp)
+                                sum += __ldcg(ws + (gp + rb) * (int64_t)(K::KC * K::BM) + e);
+                            if (c < p.k && row0 + row < p.m) C[row0 + row + (int64_t)c * p.ldc] = sum;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < K::R; ++r)
+#pragma unroll
+                for (int c = 0; c < K::KC; ++c) acc[r][c] = T(0);
+            piece_u0 = u + 1;
+        }
+        if (++jc == p.upr) { jc = 0; ++rb; }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side: compiled configurations and launch.
+
+template <class K>
+cudaError_t launch_cfg(const StreamLaunch &L, cudaStream_t stream) {
+    static std::mutex mu;
+    static uint64_t attr_done = 0;  // one bit per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < 64 && !(attr_done & (1ull << dev))) {
+            e = cudaFuncSetAttribute(stream_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM);
+            if (e != cudaSuccess) return e;
+            attr_done |= 1ull << dev;
+        }
+    }
+    Params p;
+    p.m = L.g.m;
+    p.n = L.g.n;
+    p.k = L.g.k;
+    p.B = L.g.B;
+    p.ldb = L.g.ldb;
+    p.C = L.g.C;
+    p.ldc = L.g.ldc;
+    p.ws = L.ws;
+    p.counters = L.counters;
+    p.status = L.status;
+    p.wait_ns = L.wait_ns;
+    const int64_t num_rb = (L.g.m + K::BM - 1) / K::BM;
+    p.upr = (L.g.n + K::BNS - 1) / K::BNS;
+    p.gran = K::BRES ? p.upr : 1;  // TSM2L schedule keeps row blocks whole
+    p.ngroups = num_rb * p.upr / p.gran;
+    p.c_vec = L.c_vec ? 1 : 0;
+    stream_kernel<K><<<L.grid, K::THREADS, K::SMEM, stream>>>(L.mapA, L.mapB, p);
+    return cudaGetLastError();
+}
+
+template <class K>
+StreamShape shape_of(const char *name) {
+    StreamShape s;
+    s.name = name;
+    s.elem = (int)sizeof(typename K::T);
+    s.KC = K::KC;
+    s.BM = K::BM;
+    s.BNS = K::BNS;
+    s.BOXM = K::BOXM;
+    s.gran_rows = K::BRES ? 0 : 1;
+    s.b_resident = K::BRES;
+    s.n_max_resident = K::NRES;
+    s.smem_bytes = (int)K::SMEM;
+    s.threads = K::THREADS;
+    return s;
+}
+
+// TSM2R schedule: 1 x 8 warps split the inner columns of each stage.
+//   binary32: R = 8 rows per lane (two float4), BM = 256, BNS = 32.
+//   binary64: R = 4 rows per lane (two double2), BM = 128, BNS = 32.
+template <int KC> using R32 = Cfg<float, KC, 2, 1, 8, 4, 5, false, 0>;
+template <int KC> using R64 = Cfg<double, KC, 2, 1, 8, 4, 5, false, 0>;
+// TSM2L schedule: 8 x 1 warps split the rows; B (n <= 64) resident.
+//   binary32: R = 4, BM = 1024, BNS = 8.   binary64: R = 2, BM = 512, BNS = 8.
+template <int KC> using L32 = Cfg<float, KC, 1, 8, 1, 8, 5, true, 64>;
+template <int KC> using L64 = Cfg<double, KC, 1, 8, 1, 8, 5, true, 64>;
+
+struct Entry {
+    StreamShape shape;
+    cudaError_t (*launch)(const StreamLaunch &, cudaStream_t);
+};
+
+#define TSM2_ENTRY(CFG, NAME) Entry{shape_of<CFG>(NAME), &launch_cfg<CFG>}
+
+const Entry kEntries[] = {
+    TSM2_ENTRY(R32<2>, "r_f32_kc2"),   TSM2_ENTRY(R32<4>, "r_f32_kc4"),
+    TSM2_ENTRY(R32<8>, "r_f32_kc8"),   TSM2_ENTRY(R32<16>, "r_f32_kc16"),
+    TSM2_ENTRY(R64<2>, "r_f64_kc2"),   TSM2_ENTRY(R64<4>, "r_f64_kc4"),
+    TSM2_ENTRY(R64<8>, "r_f64_kc8"),   TSM2_ENTRY(R64<16>, "r_f64_kc16"),
+    TSM2_ENTRY(L32<2>, "l_f32_kc2"),   TSM2_ENTRY(L32<4>, "l_f32_kc4"),
+    TSM2_ENTRY(L32<8>, "l_f32_kc8"),   TSM2_ENTRY(L32<16>, "l_f32_kc16"),
+    TSM2_ENTRY(L32<32>, "l_f32_kc32"), TSM2_ENTRY(L64<2>, "l_f64_kc2"),
+    TSM2_ENTRY(L64<4>, "l_f64_kc4"),   TSM2_ENTRY(L64<8>, "l_f64_kc8"),
+    TSM2_ENTRY(L64<16>, "l_f64_kc16"), TSM2_ENTRY(L64<32>, "l_f64_kc32"),
+};
+
+}  // namespace
+
+const StreamShape *stream_shape(int elem, char op, int kc) {
+    const char prefix = op == 'l' ? 'l' : 'r';
+    for (const Entry &en : kEntries)
+        if (en.shape.elem == elem && en.shape.name[0] == prefix && en.shape.KC == kc) return &en.shape;
+    return nullptr;
+}
+
+cudaError_t stream_launch(const StreamShape *shape, const StreamLaunch &L, cudaStream_t stream) {
+    for (const Entry &en : kEntries)
+        if (&en.shape == shape) return en.launch(L, stream);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace tsm2
