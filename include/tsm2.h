@@ -101,6 +101,33 @@ tsm2_status tsm2l_s(int64_t m, int64_t n, int64_t k,
                     const float *B, int64_t ldb,
                     float *C, int64_t ldc, void *stream);
 
+/* TSM2R, binary32, allocating nothing.  The paper has no counterpart: this
+ * is a library convenience.  Same arguments, result and error contract as
+ * tsm2r_s, for callers that cannot call cudaMalloc at all -- a process whose
+ * device memory is wholly owned by another allocator (a framework's caching
+ * pool that has reserved the free memory), or a latency-bound loop that
+ * cannot pay for cudaMalloc and its implicit synchronisation.
+ *  - Scratch: partial sums of row blocks split between thread blocks, and
+ *    their arrival counters, live in a fixed 16 MiB array in device memory
+ *    that every GPU loading the library holds until the process exits.  No
+ *    call of this function allocates or frees device memory.
+ *  - Limit: the partial sums must fit the array: m up to about 222,000 rows
+ *    when a column chunk is 9..16 wide, more for narrower k (the exact bound
+ *    is in the error message).  Larger problems return
+ *    TSM2_ERR_UNSUPPORTED before anything is launched.
+ *  - Set-up: the first call on each device looks up the array's device
+ *    address (cudaGetSymbolAddress) with that device current; make that first
+ *    call before any stream capture.
+ *  - Sharing: every call on a device uses the same array and it keeps the
+ *    previous call's contents; each call clears the counters it needs on its
+ *    stream.  Calls that overlap on the GPU (different streams, or other
+ *    host threads) race on the array and give undefined results; order them
+ *    on one stream or synchronise between them. */
+tsm2_status tsm2r_s_noalloc(int64_t m, int64_t n, int64_t k,
+                            const float *A, int64_t lda,
+                            const float *B, int64_t ldb,
+                            float *C, int64_t ldc, void *stream);
+
 /* Message describing the last error returned to the calling host thread
  * (thread-local; valid until that thread's next call). Never NULL. */
 const char *tsm2_get_last_error_string(void);

@@ -48,7 +48,7 @@ def _load():
             lib = ctypes.CDLL(LIB_PATH)
             i64, vp, u64 = ctypes.c_int64, ctypes.c_void_p, ctypes.c_uint64
             gemm_sig = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]
-            for name in ("tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s"):
+            for name in ("tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s", "tsm2r_s_noalloc"):
                 f = getattr(lib, name)
                 f.argtypes = gemm_sig
                 f.restype = ctypes.c_int
@@ -94,6 +94,10 @@ def tsm2l_d(m, n, k, A, lda, B, ldb, C, ldc, stream=0):
 
 def tsm2l_s(m, n, k, A, lda, B, ldb, C, ldc, stream=0):
     return _load().tsm2l_s(m, n, k, A, lda, B, ldb, C, ldc, stream)
+
+
+def tsm2r_s_noalloc(m, n, k, A, lda, B, ldb, C, ldc, stream=0):
+    return _load().tsm2r_s_noalloc(m, n, k, A, lda, B, ldb, C, ldc, stream)
 
 
 def tsm2_get_last_error_string() -> str:
@@ -186,7 +190,7 @@ def tsm2l(A, B, out=None):
 
 
 __all__ = [
-    "tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s", "tsm2_get_last_error_string", "tsm2_last_config",
+    "tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s", "tsm2r_s_noalloc", "tsm2_get_last_error_string", "tsm2_last_config",
     "tsm2_get_device_status", "tsm2_shutdown", "tsm2_set_wait_budget_ns", "tsm2_set_path", "tsm2_set_grid",
     "check", "tsm2r", "tsm2l", "empty_colmajor", "TSM2Error", "lib", "LIB_PATH",
 ]

@@ -280,6 +280,137 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
     return TSM2_SUCCESS;
 }
 
+// ---- allocation-free variant of the binary32 TSM2R bulk-copy path -----------
+//
+// Some callers cannot call cudaMalloc at all: a process whose device memory is
+// entirely owned by another allocator (for example a framework's caching pool
+// that has already reserved the free memory), or a latency-bound loop that
+// must not pay cudaMalloc's cost and implicit synchronisation.  For them,
+// tsm2r_s_noalloc keeps the partial sums of split row blocks and their
+// arrival counters in this fixed, file-scope device array instead of the
+// lazily allocated workspace.  Every GPU that loads the library holds these
+// bytes until the process exits.
+
+constexpr size_t kNoAllocScratchBytes = 16u << 20;     // 16 MiB
+constexpr size_t kNoAllocCounterBytes = 64u << 10;     // first 64 KiB: arrival counters
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64];  // device address of g_noalloc_scratch, per device
+
+// Host code may not pass g_noalloc_scratch itself to a kernel: on the host
+// that name is only a stand-in for the device array.  Its device address is
+// looked up once per device, with that device current.
+tsm2_status noalloc_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return set_error(TSM2_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return TSM2_SUCCESS;
+}
+
+tsm2_status gemm_r32_noalloc(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B,
+                             int64_t ldb, float *C, int64_t ldc, void *stream_v) {
+    const char *fn = "tsm2r_s_noalloc";
+    const int elem = 4;
+    tsm2_status st = check_args(fn, m, n, k, A, lda, B, ldb, C, ldc, elem);
+    if (st != TSM2_SUCCESS) return st;
+    if (m == 0 || k == 0) {
+        t_last_config = "empty";
+        return TSM2_SUCCESS;
+    }
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    if (n == 0) {
+        t_last_config = "zero-fill";
+        cudaError_t e = cudaMemset2DAsync(C, (size_t)ldc * elem, 0, (size_t)m * elem, (size_t)k, stream);
+        return e == cudaSuccess ? TSM2_SUCCESS : cuda_error(e, "cudaMemset2DAsync");
+    }
+    DeviceState *dev = nullptr;
+    st = device_state(&dev);
+    if (st != TSM2_SUCCESS) return st;
+    const bool a_ok = aligned16(A) && ((lda * elem) % 16 == 0) && m < (1ll << 31) - 4096 && n < (1ll << 31);
+    const bool b_ok = aligned16(B) && ((ldb * elem) % 16 == 0);
+    const bool use_stream = g_path != 1 && a_ok && b_ok;
+    void *scratch = nullptr;
+    if (use_stream) {
+        st = noalloc_scratch(&scratch);
+        if (st != TSM2_SUCCESS) return st;
+    }
+    const int kc_max = use_stream ? 16 : simple_kc_max();
+    for (int64_t c0 = 0; c0 < k; c0 += kc_max) {
+        GemmArgs g;
+        g.m = m;
+        g.n = n;
+        g.k = (int)((k - c0) < kc_max ? (k - c0) : kc_max);
+        g.A = A;
+        g.lda = lda;
+        g.B = reinterpret_cast<const char *>(B) + (size_t)c0 * ldb * elem;
+        g.ldb = ldb;
+        g.C = reinterpret_cast<char *>(C) + (size_t)c0 * ldc * elem;
+        g.ldc = ldc;
+        cudaError_t e;
+        if (!use_stream) {  // element-wise path: needs no scratch at all
+            t_last_config = "simple_f32";
+            e = simple_launch(elem, g, dev->status, stream);
+            if (e != cudaSuccess) return cuda_error(e, "simple kernel launch");
+            continue;
+        }
+        int kc = 2;
+        while (kc < g.k) kc *= 2;
+        const StreamShape *shape = stream_shape(elem, 'r', kc);
+        if (!shape) return set_error(TSM2_ERR_UNSUPPORTED, "%s: no kernel configuration for k chunk %d", fn, g.k);
+        const int64_t num_rb = (m + shape->BM - 1) / shape->BM;
+        const int64_t upr = (n + shape->BNS - 1) / shape->BNS;
+        const int64_t ngroups = num_rb * upr;
+        int64_t grid = dev->sm_count;
+        const int64_t cap = ngroups / 4;
+        if (cap < grid) grid = cap;
+        if (g_grid_override > 0) grid = g_grid_override < ngroups ? g_grid_override : ngroups;
+        if (grid > ngroups) grid = ngroups;
+        if (grid < 1) grid = 1;
+        const size_t counter_bytes = (size_t)num_rb * sizeof(int);
+        const size_t slot_bytes = (size_t)(grid + num_rb) * shape->KC * shape->BM * elem;
+        if (counter_bytes > kNoAllocCounterBytes || slot_bytes > kNoAllocScratchBytes - kNoAllocCounterBytes)
+            return set_error(TSM2_ERR_UNSUPPORTED,
+                             "%s: m=%lld needs %zu bytes of counters and %zu bytes of partial sums; the static "
+                             "scratch holds %zu and %zu (at most about %lld rows); use tsm2r_s instead",
+                             fn, (long long)m, counter_bytes, slot_bytes, kNoAllocCounterBytes,
+                             kNoAllocScratchBytes - kNoAllocCounterBytes,
+                             (long long)(((kNoAllocScratchBytes - kNoAllocCounterBytes) /
+                                          ((size_t)shape->KC * shape->BM * elem) - (size_t)grid) *
+                                         shape->BM));
+        StreamLaunch L;
+        std::memset(&L, 0, sizeof L);
+        L.g = g;
+        st = encode_2d(&L.mapA, elem, A, m, n, lda, shape->BOXM, shape->BNS);
+        if (st != TSM2_SUCCESS) return st;
+        st = encode_2d(&L.mapB, elem, g.B, n, g.k, ldb, shape->BNS, shape->KC);
+        if (st != TSM2_SUCCESS) return st;
+        // The array keeps whatever the previous call left; the arrival
+        // counters must start at zero.
+        e = cudaMemsetAsync(scratch, 0, counter_bytes, stream);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(no-alloc counters)");
+        L.grid = (int)grid;
+        L.counters = static_cast<int *>(scratch);
+        L.ws = static_cast<char *>(scratch) + kNoAllocCounterBytes;
+        L.status = dev->status;
+        L.wait_ns = g_wait_ns;
+        L.c_vec = aligned16(g.C) && ((ldc * elem) % 16 == 0);
+        t_last_config = shape->name;
+        e = stream_launch(shape, L, stream);
+        if (e != cudaSuccess) return cuda_error(e, "stream kernel launch");
+    }
+    return TSM2_SUCCESS;
+}
+
 }  // namespace
 }  // namespace tsm2
 
@@ -352,5 +483,10 @@ void tsm2_set_wait_budget_ns(int64_t ns) { g_wait_ns = ns < 0 ? 0 : ns; }
 void tsm2_set_path(int path) { g_path = path; }
 
 void tsm2_set_grid(int blocks) { g_grid_override = blocks < 0 ? 0 : blocks; }
+
+tsm2_status tsm2r_s_noalloc(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B,
+                            int64_t ldb, float *C, int64_t ldc, void *stream) {
+    return gemm_r32_noalloc(m, n, k, A, lda, B, ldb, C, ldc, stream);
+}
 
 }  // extern "C"
