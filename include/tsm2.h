@@ -157,6 +157,14 @@ void tsm2_set_path(int path);
  * SM, limited so each block gets at least a few work units). */
 void tsm2_set_grid(int blocks);
 
+/* Per-block timeline of the bulk-copy kernels, for profiling.  When set,
+ * every later launch whose grid has at most `blocks` blocks writes four
+ * 64-bit words per block b into device memory at device_words[4b..4b+3]:
+ * start time, time the first stage arrived, end time (ns, %globaltimer),
+ * and the number of work units the block processed.  NULL turns it off.
+ * The buffer is caller-owned device memory. */
+void tsm2_set_trace(unsigned long long *device_words, int64_t blocks);
+
 /* Name of the kernel configuration the last call on this thread launched
  * (for reports and tests). */
 const char *tsm2_last_config(void);

@@ -60,6 +60,8 @@ def _load():
             lib.tsm2_set_wait_budget_ns.argtypes = [i64]
             lib.tsm2_set_path.argtypes = [ctypes.c_int]
             lib.tsm2_set_grid.argtypes = [ctypes.c_int]
+            lib.tsm2_set_trace.argtypes = [vp, i64]
+            lib.tsm2_set_trace.restype = None
             for name in ("tsm2_fill_uniform_d", "tsm2_fill_uniform_s", "tsm2_fill_int_small_d",
                          "tsm2_fill_int_small_s", "tsm2_fill_logmag_s"):
                 f = getattr(lib, name)
@@ -128,6 +130,10 @@ def tsm2_set_grid(blocks: int) -> None:
     _load().tsm2_set_grid(int(blocks))
 
 
+def tsm2_set_trace(device_words, blocks: int) -> None:
+    _load().tsm2_set_trace(device_words, int(blocks))
+
+
 def check(status: int) -> None:
     """Raise :class:`TSM2Error` for a non-zero status."""
     if status != SUCCESS:
@@ -191,6 +197,6 @@ def tsm2l(A, B, out=None):
 
 __all__ = [
     "tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s", "tsm2r_s_noalloc", "tsm2_get_last_error_string", "tsm2_last_config",
-    "tsm2_get_device_status", "tsm2_shutdown", "tsm2_set_wait_budget_ns", "tsm2_set_path", "tsm2_set_grid",
+    "tsm2_get_device_status", "tsm2_shutdown", "tsm2_set_wait_budget_ns", "tsm2_set_path", "tsm2_set_grid", "tsm2_set_trace",
     "check", "tsm2r", "tsm2l", "empty_colmajor", "TSM2Error", "lib", "LIB_PATH",
 ]

@@ -32,6 +32,7 @@ struct StreamLaunch {
     int64_t wait_ns;    // bound of every pipeline wait
     int grid;           // thread blocks of the persistent grid
     bool c_vec;         // C base and ldc allow 16-byte stores
+    unsigned long long *trace;  // optional per-block timestamps (nullptr: off)
 };
 
 // Static description of a compiled stream-kernel configuration.

@@ -27,6 +27,8 @@ thread_local const char *t_last_config = "none";
 int64_t g_wait_ns = 1000000000LL;
 int g_path = 0;
 int g_grid_override = 0;
+unsigned long long *g_trace = nullptr;
+int64_t g_trace_blocks = 0;
 
 tsm2_status set_error(tsm2_status s, const char *fmt, ...) {
     char buf[512];
@@ -237,6 +239,12 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
         int kc = 2;
         while (kc < g.k) kc *= 2;
         const StreamShape *shape = stream_shape(elem, op, kc);
+        if (op == 'l') {
+            // Tall A: the 8-rows-per-lane schedule once every SM gets several
+            // of its (larger) row blocks.
+            const StreamShape *wide = stream_shape(elem, 'w', kc);
+            if (wide && (m + wide->BM - 1) / wide->BM >= 6 * (int64_t)dev->sm_count) shape = wide;
+        }
         if (!shape) return set_error(TSM2_ERR_UNSUPPORTED, "%s: no kernel configuration for k chunk %d", fn, g.k);
         StreamLaunch L;
         std::memset(&L, 0, sizeof L);
@@ -273,6 +281,7 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
         L.status = dev->status;
         L.wait_ns = g_wait_ns;
         L.c_vec = aligned16(g.C) && ((ldc * elem) % 16 == 0);
+        L.trace = (g_trace && g_trace_blocks >= grid) ? g_trace : nullptr;
         t_last_config = shape->name;
         e = stream_launch(shape, L, stream);
         if (e != cudaSuccess) return cuda_error(e, "stream kernel launch");
@@ -483,6 +492,11 @@ void tsm2_set_wait_budget_ns(int64_t ns) { g_wait_ns = ns < 0 ? 0 : ns; }
 void tsm2_set_path(int path) { g_path = path; }
 
 void tsm2_set_grid(int blocks) { g_grid_override = blocks < 0 ? 0 : blocks; }
+
+void tsm2_set_trace(unsigned long long *device_words, int64_t blocks) {
+    g_trace = device_words;
+    g_trace_blocks = device_words ? blocks : 0;
+}
 
 tsm2_status tsm2r_s_noalloc(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B,
                             int64_t ldb, float *C, int64_t ldc, void *stream) {

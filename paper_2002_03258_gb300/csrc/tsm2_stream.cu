@@ -46,10 +46,18 @@ namespace tsm2 {
 
 namespace {
 
+#ifndef TSM2_PACKED_FMA
+#define TSM2_PACKED_FMA 1
+#endif
+constexpr bool kPackedFma = TSM2_PACKED_FMA != 0;
+#ifndef TSM2_CQ
+#define TSM2_CQ 4
+#endif
+
 constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
 
-template <typename T_, int KC_, int NV_, int WR_, int WC_, int JW_, int STAGES_, bool BRES_, int NRES_>
+template <typename T_, int KC_, int NV_, int WR_, int WC_, int WK_, int JW_, int STAGES_, bool BRES_, int NRES_>
 struct Cfg {
     using T = T_;
     using VT = Vec16<T>;
@@ -59,6 +67,8 @@ struct Cfg {
     static constexpr int NV = NV_;           // 16-byte row vectors per lane
     static constexpr int WR = WR_;           // warps along rows
     static constexpr int WC = WC_;           // warps along the inner dimension
+    static constexpr int WK = WK_;           // warps along the columns of C
+    static constexpr int KCW = KC_ / WK_;    // C columns per warp
     static constexpr int JW = JW_;           // inner columns per warp per stage
     static constexpr int STAGES = STAGES_;
     static constexpr bool BRES = BRES_;      // B resident in shared memory
@@ -66,7 +76,7 @@ struct Cfg {
     static constexpr int R = NV * V;         // rows per lane
     static constexpr int BM = WR * 32 * R;   // rows per row block
     static constexpr int BNS = WC * JW;      // inner columns per stage
-    static constexpr int NW = WR * WC;       // consumer warps
+    static constexpr int NW = WR * WC * WK;  // consumer warps
     static constexpr int NT = NW * 32;       // consumer threads
     static constexpr int THREADS = NT + 128; // plus one producer warpgroup (one lane works)
     static_assert(NW == 8, "register split below assumes 2 consumer warpgroups");
@@ -74,6 +84,7 @@ struct Cfg {
     static constexpr int NBOX = BM / BOXM;
     static constexpr int JV = V;             // inner columns per B vector
     static constexpr int CC = cmin(KC, 4);   // C columns per cross-warp reduction round
+    static constexpr int CQ = cmin(KCW, TSM2_CQ);  // C columns per group of the inner loop
     static constexpr int A_STAGE = BM * BNS;                 // elements
     static constexpr int B_STAGE = BRES ? 0 : BNS * KC;      // elements
     static constexpr int RED = WC > 1 ? WC * CC * BM : 0;    // elements
@@ -85,7 +96,7 @@ struct Cfg {
     static constexpr size_t OFF_RED = OFF_BRES + (size_t)BRES_ELEMS * sizeof(T);
     static constexpr size_t OFF_BAR = align_up(OFF_RED + (size_t)RED * sizeof(T), 16);
     static constexpr size_t OFF_FLAGS = OFF_BAR + 2 * STAGES * sizeof(uint64_t);
-    static constexpr size_t SMEM = OFF_FLAGS + 16 + 128;  // + slack for 128-byte alignment
+    static constexpr size_t SMEM = OFF_FLAGS + 32 + 128;  // + slack for 128-byte alignment
 
     static_assert(JW % JV == 0, "a warp's columns must be whole B vectors");
     static_assert((BNS * sizeof(T)) % 16 == 0, "TMA inner box extent must be 16-byte multiple");
@@ -94,6 +105,7 @@ struct Cfg {
     static_assert(BM % BOXM == 0 && (32 * V) <= BOXM, "a warp's vector row group fits one box");
     static_assert(WC == 1 || (CC * BM) % NT == 0, "reduction rounds split evenly over threads");
     static_assert(!BRES || NRES % BNS == 0, "resident B covers whole stages");
+    static_assert(KC % WK == 0 && (WK == 1 || (WC == 1 && BRES)), "C columns split only in the TSM2L schedule");
     static_assert(SMEM <= 227 * 1024, "shared memory per block");
 };
 
@@ -112,6 +124,7 @@ struct Params {
     int64_t gran;     // units per indivisible group
     int64_t ngroups;  // groups in total
     int c_vec;
+    unsigned long long *trace;  // optional: 4 words per block (start, first data, end, units)
 };
 
 // Block index that owns group x under the partition gs(g) = floor(g*NG/G).
@@ -142,6 +155,10 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + K::OFF_BAR);
     uint64_t *empty = full + K::STAGES;
     volatile int *flags = reinterpret_cast<volatile int *>(smem + K::OFF_FLAGS);  // [0] abort, [1] last
+    // ldc re-read from shared memory in the epilogue, so the compiler cannot
+    // hoist per-column address offsets out of the unit loop (they would sit in
+    // registers next to the accumulators).
+    volatile int64_t *s_ldc = reinterpret_cast<volatile int64_t *>(smem + K::OFF_FLAGS + 16);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -153,12 +170,17 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     const int64_t u_end = ge * p.gran;
 
     if (threadIdx.x == 0) {
+        if (p.trace) {
+            p.trace[4 * g + 0] = globaltimer_ns();
+            p.trace[4 * g + 3] = (unsigned long long)(u_end - u_begin);
+        }
         for (int s = 0; s < K::STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], K::NW);
         }
         flags[0] = 0;
         flags[1] = 0;
+        *s_ldc = p.ldc;
         fence_mbar_init();
     }
     if constexpr (K::BRES) {
@@ -183,9 +205,11 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             int s = 0;
             uint32_t ph = 0;
             uint32_t issued = 0, last_par = 0;  // per-stage: issued at least once, parity of last issue
-            int64_t rb = u_begin / p.upr;
-            int64_t jc = u_begin - rb * p.upr;
-            for (int64_t u = u_begin; u < u_end; ++u) {
+            const int nunits = (int)(u_end - u_begin);
+            const int upr = (int)p.upr;
+            int rb = (int)(u_begin / p.upr);
+            int jc = (int)(u_begin - (int64_t)rb * p.upr);
+            for (int i = 0; i < nunits; ++i) {
                 if (flags[0]) break;
                 if (!mbar_wait_bounded(&empty[s], ph ^ 1u, p.wait_ns, flags)) {
                     flags[0] = 1;
@@ -203,7 +227,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                 issued |= 1u << s;
                 last_par = (last_par & ~(1u << s)) | (ph << s);
                 if (++s == K::STAGES) { s = 0; ph ^= 1u; }
-                if (++jc == p.upr) { jc = 0; ++rb; }
+                if (++jc == upr) { jc = 0; ++rb; }
             }
             // Let every copy this block started land before the block can exit.
             for (int t = 0; t < K::STAGES; ++t)
@@ -214,14 +238,16 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 
     // ---------------- consumers ----------------
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
-    const int cwarp = warp - 4;    // consumer warp 0 .. NW-1
-    const int wr = cwarp / K::WC;  // row group
-    const int wc = cwarp % K::WC;  // inner-column group
-    T acc[K::R][K::KC];
+    const int cwarp = warp - 4;                 // consumer warp 0 .. NW-1
+    const int wk = cwarp % K::WK;               // group of C columns
+    const int wc = (cwarp / K::WK) % K::WC;     // inner-column group
+    const int wr = cwarp / (K::WK * K::WC);     // row group
+    const int kbase = wk * K::KCW;              // first C column of this warp
+    T acc[K::R][K::KCW];
 #pragma unroll
     for (int r = 0; r < K::R; ++r)
 #pragma unroll
-        for (int c = 0; c < K::KC; ++c) acc[r][c] = T(0);
+        for (int c = 0; c < K::KCW; ++c) acc[r][c] = T(0);
 
     // Rows of the row block owned by this lane: vector v covers rows
     // row_of(v) .. row_of(v) + V - 1.
@@ -230,16 +256,21 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     int s = 0;
     uint32_t ph = 0;
     bool aborted = false;
-    int64_t rb = u_begin / p.upr;
-    int64_t jc = u_begin - rb * p.upr;
-    int64_t piece_u0 = u_begin;
+    // Unit bookkeeping in 32 bits (a block's run is far below 2^31 units;
+    // the host checks): registers are the scarce resource here.
+    const int nunits = (int)(u_end - u_begin);
+    const int upr = (int)p.upr;
+    int rb = (int)(u_begin / p.upr);
+    int jc = (int)(u_begin - (int64_t)rb * p.upr);
+    bool piece_at_rb_start = (jc == 0);
 
-    for (int64_t u = u_begin; u < u_end; ++u) {
+    for (int i = 0; i < nunits; ++i) {
         if (!aborted) {
             // Warp-uniform decision: the warp consumes the stage only if every
             // lane saw it complete.
             bool ok = !flags[0] && mbar_wait_bounded(&full[s], ph, p.wait_ns, flags);
             ok = __all_sync(0xffffffffu, ok);
+            if (p.trace && i == 0 && cwarp == 0 && lane == 0) p.trace[4 * g + 1] = globaltimer_ns();
             if (!ok) {
                 aborted = true;
                 if (lane == 0) {
@@ -275,15 +306,36 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 #pragma unroll
                         for (int e = 0; e < K::V; ++e) a[jv][v * K::V + e] = K::VT::get(x, e);
                     }
+                // C columns in groups of CQ: consecutive FMAs of a group hit
+                // different accumulators, so no FMA waits on the previous one.
 #pragma unroll
-                for (int c = 0; c < K::KC; ++c) {
-                    const vec_t bv = *reinterpret_cast<const vec_t *>(b_st + c * bstride + j);
 #pragma unroll
-                    for (int jv = 0; jv < K::JV; ++jv) {
-                        const T b = K::VT::get(bv, jv);
+                for (int c0 = 0; c0 < K::KCW; c0 += K::CQ) {
+                    vec_t bv[K::CQ];
 #pragma unroll
-                        for (int r = 0; r < K::R; ++r) acc[r][c] = fma(a[jv][r], b, acc[r][c]);
-                    }
+                    for (int cq = 0; cq < K::CQ; ++cq)
+                        bv[cq] = *reinterpret_cast<const vec_t *>(b_st + (kbase + c0 + cq) * bstride + j);
+#pragma unroll
+                    for (int jv = 0; jv < K::JV; ++jv)
+#pragma unroll
+                        for (int cq = 0; cq < K::CQ; ++cq) {
+                            const int c = c0 + cq;
+                            const T b = K::VT::get(bv[cq], jv);
+                            if constexpr (kPackedFma && sizeof(T) == 4) {
+                                // Two rows per packed FFMA2: half the FMA issue slots.
+                                const float2 bb = make_float2(b, b);
+#pragma unroll
+                                for (int r = 0; r < K::R; r += 2) {
+                                    const float2 t = __ffma2_rn(make_float2(a[jv][r], a[jv][r + 1]), bb,
+                                                                make_float2(acc[r][c], acc[r + 1][c]));
+                                    acc[r][c] = t.x;
+                                    acc[r + 1][c] = t.y;
+                                }
+                            } else {
+#pragma unroll
+                                for (int r = 0; r < K::R; ++r) acc[r][c] = fma(a[jv][r], b, acc[r][c]);
+                            }
+                        }
                 }
             }
         }
@@ -296,44 +348,57 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
         }
         if (++s == K::STAGES) { s = 0; ph ^= 1u; }
 
-        const bool rb_end = (jc == p.upr - 1);
-        if (rb_end || u == u_end - 1) {
+        const bool rb_end = (jc == upr - 1);
+        if (rb_end || i == nunits - 1) {
             // ---------------- epilogue of one piece of row block rb ----------------
-            const int64_t rb_u0 = rb * p.upr;
-            const bool whole = (piece_u0 == rb_u0) && rb_end;
-            const int64_t row0 = rb * K::BM;
+            const int64_t rb64 = rb;
+            const int64_t rb_u0 = rb64 * p.upr;
+            // TSM2L runs are whole row blocks by construction (gran = upr).
+            const bool whole = K::BRES || (piece_at_rb_start && rb_end);
+            const int64_t row0 = rb64 * K::BM;
             T *C = static_cast<T *>(p.C);
             T *ws = static_cast<T *>(p.ws);
             const int64_t NG = p.ngroups;
             const int64_t gA = owner_of(rb_u0 / p.gran, G, NG);
             const int64_t gB = owner_of((rb_u0 + p.upr - 1) / p.gran, G, NG);
-            const int64_t my_slot = g + rb;
+            const int64_t my_slot = g + rb64;
             const int tid = threadIdx.x - 128;  // 0 .. NT-1 for consumers
 
             if constexpr (K::WC == 1) {
                 if (whole) {
                     if (!aborted) {
+                        // Fast path: the row block lies inside C, all its columns are
+                        // live and C allows 16-byte stores: unpredicated vector stores.
+                        const bool fast = p.c_vec && row0 + K::BM <= p.m && kbase + K::KCW <= p.k;
+                        const int64_t ldc = *s_ldc;
+                        T *cw = C + row0 + (int64_t)kbase * ldc;
+                        if (fast) {
 #pragma unroll
-                        for (int v = 0; v < K::NV; ++v) {
-                            const int64_t r0 = row0 + row_of(v);
+                            for (int c = 0; c < K::KCW; ++c) {
 #pragma unroll
-                            for (int c = 0; c < K::KC; ++c) {
-                                if (c >= p.k) continue;
-                                T *dst = C + r0 + (int64_t)c * p.ldc;
-                                if (p.c_vec && r0 + K::V <= p.m) {
+                                for (int v = 0; v < K::NV; ++v) {
                                     T tmp[K::V];
 #pragma unroll
                                     for (int e = 0; e < K::V; ++e) tmp[e] = acc[v * K::V + e][c];
-                                    *reinterpret_cast<vec_t *>(dst) = K::VT::make(tmp);
-                                } else {
-#pragma unroll
-                                    for (int e = 0; e < K::V; ++e)
-                                        if (r0 + e < p.m) dst[e] = acc[v * K::V + e][c];
+                                    *reinterpret_cast<vec_t *>(cw + row_of(v)) = K::VT::make(tmp);
                                 }
+                                cw += ldc;
+                            }
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < K::KCW; ++c) {
+                                if (kbase + c < p.k) {
+#pragma unroll
+                                    for (int v = 0; v < K::NV; ++v)
+#pragma unroll
+                                        for (int e = 0; e < K::V; ++e)
+                                            if (row0 + row_of(v) + e < p.m) cw[row_of(v) + e] = acc[v * K::V + e][c];
+                                }
+                                cw += ldc;
                             }
                         }
                     }
-                } else {
+                } else if constexpr (!K::BRES) {
                     // Partial sums in registers -> slot [KC][BM] at this lane's rows.
                     T *slot = ws + my_slot * (int64_t)(K::KC * K::BM);
 #pragma unroll
@@ -382,7 +447,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                 }
             }
 
-            if (!whole) {
+            if (!K::BRES && !whole) {
                 // Publish this piece; the last arriving block of the row block
                 // adds all pieces in block order and writes C.
                 __threadfence();
@@ -408,7 +473,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                                 T sum[K::V];
                                 for (int64_t gp = gA; gp <= gB; ++gp) {
                                     const vec_t x = __ldcg(reinterpret_cast<const vec_t *>(
-                                        ws + (gp + rb) * (int64_t)(K::KC * K::BM) + c * K::BM + row_of(v)));
+                                        ws + (gp + rb64) * (int64_t)(K::KC * K::BM) + c * K::BM + row_of(v)));
 #pragma unroll
                                     for (int e = 0; e < K::V; ++e)
                                         sum[e] = (gp == gA) ? K::VT::get(x, e) : sum[e] + K::VT::get(x, e);
@@ -420,13 +485,27 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                                         if (r0 + e < p.m) C[r0 + e + (int64_t)c * p.ldc] = sum[e];
                             }
                     } else {
-                        for (int e = tid; e < K::KC * K::BM; e += K::NT) {
+                        // All of a piece's loads are issued together (independent
+                        // L2 round trips in flight), pieces added in block order.
+                        constexpr int E = (K::KC * K::BM) / K::NT;
+                        T sum[E];
+                        const T *src = ws + (gA + rb64) * (int64_t)(K::KC * K::BM) + tid;
+#pragma unroll
+                        for (int q = 0; q < E; ++q) sum[q] = __ldcg(src + q * K::NT);
+                        for (int64_t gp = gA + 1; gp <= gB; ++gp) {
+                            src += K::KC * K::BM;
+                            T x[E];
+#pragma unroll
+                            for (int q = 0; q < E; ++q) x[q] = __ldcg(src + q * K::NT);
+#pragma unroll
+                            for (int q = 0; q < E; ++q) sum[q] += x[q];
+                        }
+#pragma unroll
+                        for (int q = 0; q < E; ++q) {
+                            const int e = tid + q * K::NT;
                             const int c = e / K::BM;
                             const int row = e - c * K::BM;
-                            T sum = __ldcg(ws + (gA + rb) * (int64_t)(K::KC * K::BM) + e);
-                            for (int64_t gp = gA + 1; gp <= gB; ++gp)
-                                sum += __ldcg(ws + (gp + rb) * (int64_t)(K::KC * K::BM) + e);
-                            if (c < p.k && row0 + row < p.m) C[row0 + row + (int64_t)c * p.ldc] = sum;
+                            if (c < p.k && row0 + row < p.m) C[row0 + row + (int64_t)c * p.ldc] = sum[q];
                         }
                     }
                 }
@@ -434,11 +513,12 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 #pragma unroll
             for (int r = 0; r < K::R; ++r)
 #pragma unroll
-                for (int c = 0; c < K::KC; ++c) acc[r][c] = T(0);
-            piece_u0 = u + 1;
+                for (int c = 0; c < K::KCW; ++c) acc[r][c] = T(0);
+            piece_at_rb_start = true;
         }
-        if (++jc == p.upr) { jc = 0; ++rb; }
+        if (++jc == upr) { jc = 0; ++rb; }
     }
+    if (p.trace && threadIdx.x == 128) p.trace[4 * g + 2] = globaltimer_ns();
 }
 
 // ---------------------------------------------------------------------------
@@ -476,6 +556,7 @@ cudaError_t launch_cfg(const StreamLaunch &L, cudaStream_t stream) {
     p.gran = K::BRES ? p.upr : 1;  // TSM2L schedule keeps row blocks whole
     p.ngroups = num_rb * p.upr / p.gran;
     p.c_vec = L.c_vec ? 1 : 0;
+    p.trace = L.trace;
     stream_kernel<K><<<L.grid, K::THREADS, K::SMEM, stream>>>(L.mapA, L.mapB, p);
     return cudaGetLastError();
 }
@@ -500,38 +581,50 @@ StreamShape shape_of(const char *name) {
 // TSM2R schedule: 1 x 8 warps split the inner columns of each stage.
 //   binary32: R = 8 rows per lane (two float4), BM = 256, BNS = 32.
 //   binary64: R = 4 rows per lane (two double2), BM = 128, BNS = 32.
-template <int KC> using R32 = Cfg<float, KC, 2, 1, 8, 4, 5, false, 0>;
-template <int KC> using R64 = Cfg<double, KC, 2, 1, 8, 4, 5, false, 0>;
+template <int KC> using R32 = Cfg<float, KC, 2, 1, 8, 1, 4, 5, false, 0>;
+template <int KC> using R64 = Cfg<double, KC, 2, 1, 8, 1, 4, 5, false, 0>;
 // TSM2L schedule: 8 x 1 warps split the rows; B (n <= 64) resident.
 //   binary32: R = 4, BM = 1024, BNS = 8.   binary64: R = 2, BM = 512, BNS = 8.
-template <int KC> using L32 = Cfg<float, KC, 1, 8, 1, 8, 5, true, 64>;
-template <int KC> using L64 = Cfg<double, KC, 1, 8, 1, 8, 5, true, 64>;
+//   KC = 32 splits the C columns over 2 x 4 warps (16 accumulated columns per
+//   lane, BM halves) to keep the accumulators in registers.
+template <int KC> using L32 = Cfg<float, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, 5, true, 64>;
+template <int KC> using L64 = Cfg<double, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, 5, true, 64>;
+// TSM2L schedule for tall A (binary32): R = 8 rows per lane, so every B value
+// read from shared memory (one wavefront per broadcast value) feeds twice the
+// FMAs; the C columns are split over WK = 1, 2, 4 warps (KC <= 8, 16, 32) so a
+// lane never holds more than 64 accumulators.  Chosen when there are enough
+// row blocks for an even spread over the SMs.
+template <int KC> using W32 = Cfg<float, KC, 2, (KC >= 32 ? 2 : KC >= 16 ? 4 : 8), 1, (KC >= 32 ? 4 : KC >= 16 ? 2 : 1),
+                                  (KC >= 16 ? 8 : 4), 5, true, 64>;
 
 struct Entry {
+    char op;  // 'r': TSM2R schedule, 'l': TSM2L, 'w': TSM2L with 8 rows per lane
     StreamShape shape;
     cudaError_t (*launch)(const StreamLaunch &, cudaStream_t);
 };
 
-#define TSM2_ENTRY(CFG, NAME) Entry{shape_of<CFG>(NAME), &launch_cfg<CFG>}
+#define TSM2_ENTRY(OP, CFG, NAME) Entry{OP, shape_of<CFG>(NAME), &launch_cfg<CFG>}
 
 const Entry kEntries[] = {
-    TSM2_ENTRY(R32<2>, "r_f32_kc2"),   TSM2_ENTRY(R32<4>, "r_f32_kc4"),
-    TSM2_ENTRY(R32<8>, "r_f32_kc8"),   TSM2_ENTRY(R32<16>, "r_f32_kc16"),
-    TSM2_ENTRY(R64<2>, "r_f64_kc2"),   TSM2_ENTRY(R64<4>, "r_f64_kc4"),
-    TSM2_ENTRY(R64<8>, "r_f64_kc8"),   TSM2_ENTRY(R64<16>, "r_f64_kc16"),
-    TSM2_ENTRY(L32<2>, "l_f32_kc2"),   TSM2_ENTRY(L32<4>, "l_f32_kc4"),
-    TSM2_ENTRY(L32<8>, "l_f32_kc8"),   TSM2_ENTRY(L32<16>, "l_f32_kc16"),
-    TSM2_ENTRY(L32<32>, "l_f32_kc32"), TSM2_ENTRY(L64<2>, "l_f64_kc2"),
-    TSM2_ENTRY(L64<4>, "l_f64_kc4"),   TSM2_ENTRY(L64<8>, "l_f64_kc8"),
-    TSM2_ENTRY(L64<16>, "l_f64_kc16"), TSM2_ENTRY(L64<32>, "l_f64_kc32"),
+    TSM2_ENTRY('r', R32<2>, "r_f32_kc2"),   TSM2_ENTRY('r', R32<4>, "r_f32_kc4"),
+    TSM2_ENTRY('r', R32<8>, "r_f32_kc8"),   TSM2_ENTRY('r', R32<16>, "r_f32_kc16"),
+    TSM2_ENTRY('r', R64<2>, "r_f64_kc2"),   TSM2_ENTRY('r', R64<4>, "r_f64_kc4"),
+    TSM2_ENTRY('r', R64<8>, "r_f64_kc8"),   TSM2_ENTRY('r', R64<16>, "r_f64_kc16"),
+    TSM2_ENTRY('l', L32<2>, "l_f32_kc2"),   TSM2_ENTRY('l', L32<4>, "l_f32_kc4"),
+    TSM2_ENTRY('l', L32<8>, "l_f32_kc8"),   TSM2_ENTRY('l', L32<16>, "l_f32_kc16"),
+    TSM2_ENTRY('l', L32<32>, "l_f32_kc32"), TSM2_ENTRY('l', L64<2>, "l_f64_kc2"),
+    TSM2_ENTRY('l', L64<4>, "l_f64_kc4"),   TSM2_ENTRY('l', L64<8>, "l_f64_kc8"),
+    TSM2_ENTRY('l', L64<16>, "l_f64_kc16"), TSM2_ENTRY('l', L64<32>, "l_f64_kc32"),
+    TSM2_ENTRY('w', W32<2>, "lw_f32_kc2"),  TSM2_ENTRY('w', W32<4>, "lw_f32_kc4"),
+    TSM2_ENTRY('w', W32<8>, "lw_f32_kc8"),  TSM2_ENTRY('w', W32<16>, "lw_f32_kc16"),
+    TSM2_ENTRY('w', W32<32>, "lw_f32_kc32"),
 };
 
 }  // namespace
 
 const StreamShape *stream_shape(int elem, char op, int kc) {
-    const char prefix = op == 'l' ? 'l' : 'r';
     for (const Entry &en : kEntries)
-        if (en.shape.elem == elem && en.shape.name[0] == prefix && en.shape.KC == kc) return &en.shape;
+        if (en.shape.elem == elem && en.op == op && en.shape.KC == kc) return &en.shape;
     return nullptr;
 }
 

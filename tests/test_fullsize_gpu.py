@@ -44,6 +44,11 @@ def device_matrix(rows, cols, dtype, seed, mid, dist="uniform"):
     ("l", np.float32, 2 ** 20, 8, 8, "int_small"),
     ("l", np.float64, 2 ** 23, 16, 16, "uniform"),
     ("l", np.float64, 2 ** 20, 32, 32, "uniform"),
+    # the 8-rows-per-lane TSM2L schedule (selected for tall A)
+    ("l", np.float32, 3_000_000, 8, 8, "uniform"),
+    ("l", np.float32, 3_000_000, 16, 16, "uniform"),
+    ("l", np.float32, 3_000_000, 20, 20, "int_small"),
+    ("l", np.float32, 3_000_000, 32, 32, "uniform"),
 ])
 def test_fullsize_sampled_rows(op, dtype, m, n, k, dist):
     import paper_2002_03258_gb300 as pkg
@@ -56,7 +61,10 @@ def test_fullsize_sampled_rows(op, dtype, m, n, k, dist):
     st = fn(m, n, k, A.data_ptr(), m, B.data_ptr(), n, C.data_ptr(), m, 0)
     assert st == 0, pkg.tsm2_get_last_error_string()
     assert pkg.tsm2_get_device_status(0) == 0
-    assert not pkg.tsm2_last_config().startswith("simple")
+    cfg = pkg.tsm2_last_config()
+    assert not cfg.startswith("simple")
+    if op == "l" and dtype == np.float32 and m >= 3_000_000:
+        assert cfg.startswith("lw_"), cfg
     rows = sample_rows(m)
     got = C[torch.from_numpy(rows).cuda()].cpu().numpy()
     gen = {"uniform": ti.uniform_pm1, "int_small": ti.int_small}[dist]
