@@ -83,7 +83,7 @@ def measured_peaks():
 
 
 def traffic_record(config_name, workload_key):
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(p):
         return None
     try:
@@ -439,6 +439,47 @@ def run_gpu(args):
     return 0
 
 
+def run_case(args):
+    """One multiply, timed like the sweep (for profiling single kernels)."""
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2002_03258_gb300 as pkg
+    import tsm2_inputs as ti
+    op, dt, m, n, k = args.case.split(":")
+    m, n, k = int(m), int(n), int(k)
+    tdt = torch.float32 if dt == "f32" else torch.float64
+    suf = "s" if dt == "f32" else "d"
+    es = 4 if dt == "f32" else 8
+    lib = pkg.lib()
+    A = torch.empty((n, m), dtype=tdt, device="cuda").t()
+    B = torch.empty((k, n), dtype=tdt, device="cuda").t()
+    C = torch.empty((k, m), dtype=tdt, device="cuda").t()
+    fill = getattr(lib, f"tsm2_fill_uniform_{suf}")
+    pkg.check(fill(m, n, 0, ti.MID_A, A.data_ptr(), m, 0))
+    pkg.check(fill(n, k, 0, ti.MID_B, B.data_ptr(), n, 0))
+    l2 = getattr(torch.cuda.get_device_properties(0), "L2_cache_size", 128 << 20) or (128 << 20)
+    flush = torch.empty(2 * l2, dtype=torch.uint8, device="cuda")
+    fn = getattr(pkg, f"tsm2{op}_{suf}")
+    ts = []
+    for r in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pkg.check(fn(m, n, k, A.data_ptr(), m, B.data_ptr(), n, C.data_ptr(), m, 0))
+        e1.record()
+        torch.cuda.synchronize()
+        if r >= args.warmup:
+            ts.append(e0.elapsed_time(e1))
+    pkg.check(pkg.tsm2_get_device_status(0))
+    ms = statistics.median(ts)
+    print(json.dumps({"case": args.case, "config": pkg.tsm2_last_config(), "ms": round(ms, 4),
+                      "gbs": round(alg_bytes(m, n, k, es) / (ms * 1e-3) / 1e9, 1),
+                      "algorithmic_bytes": alg_bytes(m, n, k, es), "src_hash": src_hash()}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -448,7 +489,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cublas", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--case", default=None, help="op:dtype:m:n:k, e.g. r:f32:8192:8192:16 -- time one multiply only")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
