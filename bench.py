@@ -379,6 +379,49 @@ def run_gpu(args):
         del bufs64, work64
         torch.cuda.empty_cache()
 
+    # ---- differentiable TSM2R: forward + backward (binary32, 16384^2, k = 8) -------------------
+    fwd_bwd = None
+    if not args.no_fwdbwd:
+        m = n = 16384
+        k = 8
+        sc = 1.0 / (n ** 0.5)
+        A = torch.empty((n, m), dtype=torch.float32, device=dev).t()
+        B = torch.empty((k, n), dtype=torch.float32, device=dev).t()
+        dC = torch.empty((k, m), dtype=torch.float32, device=dev).t()
+        C = torch.empty((k, m), dtype=torch.float32, device=dev).t()
+        dB = torch.empty((k, n), dtype=torch.float32, device=dev).t()
+        dA = torch.empty((n, m), dtype=torch.float32, device=dev).t()
+        pkg.check(lib.tsm2_fill_normal_ih_s(m, n, 0, ti.MID_A, sc, A.data_ptr(), m, sh))
+        pkg.check(lib.tsm2_fill_normal_ih_s(n, k, 0, ti.MID_B, sc, B.data_ptr(), n, sh))
+        pkg.check(lib.tsm2_fill_normal_ih_s(m, k, 0, ti.MID_DC, 1.0, dC.data_ptr(), m, sh))
+        legs = {
+            "fwd": lambda: pkg.tsm2r_s(m, n, k, A.data_ptr(), m, B.data_ptr(), n, C.data_ptr(), m, sh),
+            "dB": lambda: pkg.tsm2r_t_s(m, n, k, A.data_ptr(), m, dC.data_ptr(), m, dB.data_ptr(), n, sh),
+            "dA": lambda: pkg.tsm2_rankk_s(m, n, k, dC.data_ptr(), m, B.data_ptr(), n, dA.data_ptr(), m, sh),
+        }
+        leg_bytes = 4 * (m * n + n * k + m * k)
+        times = {}
+        for name, f in legs.items():
+            ts = []
+            for r in range(args.warmup + max(3, min(args.steps, 10))):
+                l2_flush()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pkg.check(f())
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if r >= args.warmup:
+                    ts.append(e0.elapsed_time(e1))
+            times[name] = statistics.median(ts)
+        pkg.check(pkg.tsm2_get_device_status(sh))
+        tot = sum(times.values())
+        fwd_bwd = {"workload": "16384 x 16384 x 8 binary32, N(0,1/n) inputs, dC N(0,1)",
+                   "ms": {kk: round(v, 4) for kk, v in times.items()}, "total_ms": round(tot, 4),
+                   "gbs": {kk: round(leg_bytes / (v * 1e-3) / 1e9, 1) for kk, v in times.items()},
+                   "frac_hbm": {kk: round(leg_bytes / (v * 1e-3) / 1e9 / peak_hbm, 3) for kk, v in times.items()},
+                   "fwd_bwd_over_fwd": round(tot / times["fwd"], 3)}
+        del A, B, dC, C, dB, dA
+
     # ---- end to end through the C ABI with host buffers --------------------------------------
     h_in, h_out = [], []
     for w in work32:
@@ -430,7 +473,7 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "step_wall_s": round(wall / args.steps, 4)},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
-        "clocks": clock_rec, "fp64": fp64, "cases": case_rows, "src_hash": src_hash(),
+        "clocks": clock_rec, "fp64": fp64, "fwd_bwd": fwd_bwd, "cases": case_rows, "src_hash": src_hash(),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -489,6 +532,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cublas", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fwdbwd", action="store_true")
     ap.add_argument("--case", default=None, help="op:dtype:m:n:k, e.g. r:f32:8192:8192:16 -- time one multiply only")
     args = ap.parse_args()
     if args.case:

@@ -101,6 +101,29 @@ tsm2_status tsm2l_s(int64_t m, int64_t n, int64_t k,
                     const float *B, int64_t ldb,
                     float *C, int64_t ldc, void *stream);
 
+/* ---- Backward products of C = A B (gradients for a differentiable TSM2R) -- */
+
+/* dB(n x k) = A^T dC, A m x n (lda >= max(1,m)), dC m x k (lddc >= max(1,m)),
+ * dB n x k (lddb >= max(1,n)); dB is overwritten.  The reduction runs along
+ * the m rows of A, each of which is read once per group of up to 16 columns
+ * of dC (the outer-product principle of Algorithm 2, Sec. 3.1.2, applied to
+ * the transposed product).  m == 0 sets dB to zero.  Same pointer, stream,
+ * alignment, accuracy (gamma_m |A^T||dC|), scratch and error contract as
+ * tsm2r_d. */
+tsm2_status tsm2r_t_d(int64_t m, int64_t n, int64_t k, const double *A, int64_t lda,
+                      const double *dC, int64_t lddc, double *dB, int64_t lddb, void *stream);
+tsm2_status tsm2r_t_s(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda,
+                      const float *dC, int64_t lddc, float *dB, int64_t lddb, void *stream);
+
+/* dA(m x n) = dC B^T, dC m x k (lddc >= max(1,m)), B n x k (ldb >= max(1,n)),
+ * dA m x n (ldda >= max(1,m)); dA is overwritten (k == 0 sets it to zero).
+ * A rank-k update: dA is written once, as a stream.  For k > 16 the columns of
+ * dC and B are processed in groups of 16 and later groups add into dA. */
+tsm2_status tsm2_rankk_d(int64_t m, int64_t n, int64_t k, const double *dC, int64_t lddc,
+                         const double *B, int64_t ldb, double *dA, int64_t ldda, void *stream);
+tsm2_status tsm2_rankk_s(int64_t m, int64_t n, int64_t k, const float *dC, int64_t lddc,
+                         const float *B, int64_t ldb, float *dA, int64_t ldda, void *stream);
+
 /* TSM2R, binary32, allocating nothing.  The paper has no counterpart: this
  * is a library convenience.  Same arguments, result and error contract as
  * tsm2r_s, for callers that cannot call cudaMalloc at all -- a process whose

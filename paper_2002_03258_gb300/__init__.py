@@ -52,6 +52,10 @@ def _load():
                 f = getattr(lib, name)
                 f.argtypes = gemm_sig
                 f.restype = ctypes.c_int
+            for name in ("tsm2r_t_d", "tsm2r_t_s", "tsm2_rankk_d", "tsm2_rankk_s"):
+                f = getattr(lib, name)
+                f.argtypes = gemm_sig
+                f.restype = ctypes.c_int
             lib.tsm2_get_last_error_string.restype = ctypes.c_char_p
             lib.tsm2_last_config.restype = ctypes.c_char_p
             lib.tsm2_get_device_status.argtypes = [vp]
@@ -100,6 +104,22 @@ def tsm2l_s(m, n, k, A, lda, B, ldb, C, ldc, stream=0):
 
 def tsm2r_s_noalloc(m, n, k, A, lda, B, ldb, C, ldc, stream=0):
     return _load().tsm2r_s_noalloc(m, n, k, A, lda, B, ldb, C, ldc, stream)
+
+
+def tsm2r_t_d(m, n, k, A, lda, dC, lddc, dB, lddb, stream=0):
+    return _load().tsm2r_t_d(m, n, k, A, lda, dC, lddc, dB, lddb, stream)
+
+
+def tsm2r_t_s(m, n, k, A, lda, dC, lddc, dB, lddb, stream=0):
+    return _load().tsm2r_t_s(m, n, k, A, lda, dC, lddc, dB, lddb, stream)
+
+
+def tsm2_rankk_d(m, n, k, dC, lddc, B, ldb, dA, ldda, stream=0):
+    return _load().tsm2_rankk_d(m, n, k, dC, lddc, B, ldb, dA, ldda, stream)
+
+
+def tsm2_rankk_s(m, n, k, dC, lddc, B, ldb, dA, ldda, stream=0):
+    return _load().tsm2_rankk_s(m, n, k, dC, lddc, B, ldb, dA, ldda, stream)
 
 
 def tsm2_get_last_error_string() -> str:
@@ -185,6 +205,40 @@ def _matmul(op, A, B, out=None):
     return out
 
 
+def tsm2r_t(A, dC, out=None):
+    """dB = A^T @ dC (A m x n, dC m x k; column-major views), the transposed TSM2R."""
+    import torch
+    if A.dtype != dC.dtype or A.dtype not in (torch.float32, torch.float64):
+        raise TypeError("A and dC must both be float32 or both float64")
+    m, n, lda = _colmajor(A, "A")
+    m2, k, lddc = _colmajor(dC, "dC")
+    if m != m2:
+        raise ValueError(f"row counts differ: {A.shape} vs {dC.shape}")
+    if out is None:
+        out = empty_colmajor(n, k, A.dtype, A.device)
+    _, _, lddb = _colmajor(out, "out")
+    fn = tsm2r_t_d if A.dtype == torch.float64 else tsm2r_t_s
+    check(fn(m, n, k, A.data_ptr(), lda, dC.data_ptr(), lddc, out.data_ptr(), lddb, _stream_of(A)))
+    return out
+
+
+def rankk(dC, B, out=None):
+    """dA = dC @ B^T (dC m x k, B n x k; column-major views), a rank-k update."""
+    import torch
+    if dC.dtype != B.dtype or dC.dtype not in (torch.float32, torch.float64):
+        raise TypeError("dC and B must both be float32 or both float64")
+    m, k, lddc = _colmajor(dC, "dC")
+    n, k2, ldb = _colmajor(B, "B")
+    if k != k2:
+        raise ValueError(f"column counts differ: {dC.shape} vs {B.shape}")
+    if out is None:
+        out = empty_colmajor(m, n, dC.dtype, dC.device)
+    _, _, ldda = _colmajor(out, "out")
+    fn = tsm2_rankk_d if dC.dtype == torch.float64 else tsm2_rankk_s
+    check(fn(m, n, k, dC.data_ptr(), lddc, B.data_ptr(), ldb, out.data_ptr(), ldda, _stream_of(dC)))
+    return out
+
+
 def tsm2r(A, B, out=None):
     """C = A @ B with the TSM2R schedule (large A, tall-and-skinny B)."""
     return _matmul("r", A, B, out)
@@ -198,5 +252,6 @@ def tsm2l(A, B, out=None):
 __all__ = [
     "tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s", "tsm2r_s_noalloc", "tsm2_get_last_error_string", "tsm2_last_config",
     "tsm2_get_device_status", "tsm2_shutdown", "tsm2_set_wait_budget_ns", "tsm2_set_path", "tsm2_set_grid", "tsm2_set_trace",
-    "check", "tsm2r", "tsm2l", "empty_colmajor", "TSM2Error", "lib", "LIB_PATH",
+    "check", "tsm2r", "tsm2l", "tsm2r_t", "rankk", "empty_colmajor", "TSM2Error", "lib", "LIB_PATH",
+    "tsm2r_t_d", "tsm2r_t_s", "tsm2_rankk_d", "tsm2_rankk_s",
 ]

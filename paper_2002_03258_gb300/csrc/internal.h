@@ -59,6 +59,34 @@ cudaError_t stream_launch(const StreamShape *shape, const StreamLaunch &L, cudaS
 cudaError_t simple_launch(int elem, const GemmArgs &g, unsigned *status, cudaStream_t stream);
 int simple_kc_max();
 
+// ---- backward products ----------------------------------------------------
+
+// dB = A^T dC with the bulk-copy pipeline (tsm2_backward.cu).
+struct TLaunch {
+    int64_t m, n;
+    int k;           // live columns of dC / dB in this chunk (<= KC)
+    CUtensorMap mapA;  // A: dims {m, n}, box {BOXM, BNS}
+    CUtensorMap mapD;  // dC: dims {m, k}, box {BOXM, KC}
+    void *dB;
+    int64_t lddb;
+    void *ws;
+    int *counters;
+    unsigned *status;
+    int64_t wait_ns;
+    int grid;
+};
+struct TShape {
+    const char *name;
+    int elem, KC, BM, BNS, BOXM;
+};
+const TShape *tsm2t_shape(int elem, int kc);
+cudaError_t tsm2t_launch(const TShape *shape, const TLaunch &L, cudaStream_t stream);
+cudaError_t simple_t_launch(int elem, int64_t m, int64_t n, int k, const void *A, int64_t lda, const void *dC,
+                            int64_t lddc, void *dB, int64_t lddb, cudaStream_t stream);
+cudaError_t rankk_launch(int elem, int64_t m, int64_t n, int k, const void *dC, int64_t lddc, const void *B,
+                         int64_t ldb, void *dA, int64_t ldda, bool vec_ok, bool accumulate, int sm_count,
+                         cudaStream_t stream);
+
 // Work partition of the persistent grid (shared by host sizing and kernels).
 struct Partition {
     int64_t num_rb;  // row blocks

@@ -289,6 +289,137 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
     return TSM2_SUCCESS;
 }
 
+// ---- backward products ------------------------------------------------------
+
+tsm2_status gemm_t(const char *fn, int elem, int64_t m, int64_t n, int64_t k, const void *A, int64_t lda,
+                   const void *dC, int64_t lddc, void *dB, int64_t lddb, void *stream_v) {
+    if (m < 0 || n < 0 || k < 0)
+        return set_error(TSM2_ERR_INVALID_VALUE, "%s: negative dimension (m=%lld n=%lld k=%lld)", fn, (long long)m,
+                         (long long)n, (long long)k);
+    if (lda < (m > 1 ? m : 1)) return set_error(TSM2_ERR_INVALID_VALUE, "%s: lda=%lld < max(1,m)", fn, (long long)lda);
+    if (lddc < (m > 1 ? m : 1))
+        return set_error(TSM2_ERR_INVALID_VALUE, "%s: lddc=%lld < max(1,m)", fn, (long long)lddc);
+    if (lddb < (n > 1 ? n : 1))
+        return set_error(TSM2_ERR_INVALID_VALUE, "%s: lddb=%lld < max(1,n)", fn, (long long)lddb);
+    if (n > 0 && k > 0 && dB == nullptr) return set_error(TSM2_ERR_INVALID_VALUE, "%s: dB is NULL", fn);
+    if (m > 0 && n > 0 && k > 0 && (A == nullptr || dC == nullptr))
+        return set_error(TSM2_ERR_INVALID_VALUE, "%s: A or dC is NULL", fn);
+    if (n > 0 && k > 0 && m > 0) {
+        const size_t ob = span_bytes(n, k, lddb, elem);
+        if (ranges_overlap(dB, ob, A, span_bytes(m, n, lda, elem)) ||
+            ranges_overlap(dB, ob, dC, span_bytes(m, k, lddc, elem)))
+            return set_error(TSM2_ERR_INVALID_VALUE, "%s: dB overlaps A or dC", fn);
+    }
+    if (n == 0 || k == 0) {
+        t_last_config = "empty";
+        return TSM2_SUCCESS;
+    }
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    if (m == 0) {
+        t_last_config = "zero-fill";
+        cudaError_t e = cudaMemset2DAsync(dB, (size_t)lddb * elem, 0, (size_t)n * elem, (size_t)k, stream);
+        return e == cudaSuccess ? TSM2_SUCCESS : cuda_error(e, "cudaMemset2DAsync");
+    }
+    DeviceState *dev = nullptr;
+    tsm2_status st = device_state(&dev);
+    if (st != TSM2_SUCCESS) return st;
+    const bool ok = g_path != 1 && aligned16(A) && aligned16(dC) && (lda * elem) % 16 == 0 &&
+                    (lddc * elem) % 16 == 0 && m < (1ll << 31) - 4096 && n < (1ll << 31);
+    for (int64_t c0 = 0; c0 < k; c0 += 16) {
+        const int kk = (int)((k - c0) < 16 ? (k - c0) : 16);
+        const void *dCc = static_cast<const char *>(dC) + (size_t)c0 * lddc * elem;
+        void *dBc = static_cast<char *>(dB) + (size_t)c0 * lddb * elem;
+        cudaError_t e;
+        if (!ok) {
+            t_last_config = elem == 8 ? "simple_t_f64" : "simple_t_f32";
+            e = simple_t_launch(elem, m, n, kk, A, lda, dCc, lddc, dBc, lddb, stream);
+            if (e != cudaSuccess) return cuda_error(e, "simple_t kernel launch");
+            continue;
+        }
+        int kc = 2;
+        while (kc < kk) kc *= 2;
+        const TShape *shape = tsm2t_shape(elem, kc);
+        if (!shape) return set_error(TSM2_ERR_UNSUPPORTED, "%s: no configuration for k chunk %d", fn, kk);
+        TLaunch L;
+        std::memset(&L, 0, sizeof L);
+        L.m = m;
+        L.n = n;
+        L.k = kk;
+        st = encode_2d(&L.mapA, elem, A, m, n, lda, shape->BOXM, shape->BNS);
+        if (st != TSM2_SUCCESS) return st;
+        st = encode_2d(&L.mapD, elem, dCc, m, kk, lddc, shape->BOXM, shape->KC);
+        if (st != TSM2_SUCCESS) return st;
+        const int64_t nrb = (m + shape->BM - 1) / shape->BM;
+        const int64_t nch = (n + shape->BNS - 1) / shape->BNS;
+        const int64_t nunits = nrb * nch;
+        int64_t grid = dev->sm_count;
+        if (nunits / 4 < grid) grid = nunits / 4;
+        if (g_grid_override > 0) grid = g_grid_override;
+        if (grid > nunits) grid = nunits;
+        if (grid < 1) grid = 1;
+        void *ws = nullptr;
+        int *counters = nullptr;
+        st = workspace(stream, (size_t)nch * sizeof(int), (size_t)(grid + nch) * shape->BNS * shape->KC * elem, &ws,
+                       &counters);
+        if (st != TSM2_SUCCESS) return st;
+        L.dB = dBc;
+        L.lddb = lddb;
+        L.ws = ws;
+        L.counters = counters;
+        L.status = dev->status;
+        L.wait_ns = g_wait_ns;
+        L.grid = (int)grid;
+        t_last_config = shape->name;
+        e = tsm2t_launch(shape, L, stream);
+        if (e != cudaSuccess) return cuda_error(e, "transposed kernel launch");
+    }
+    return TSM2_SUCCESS;
+}
+
+tsm2_status rankk(const char *fn, int elem, int64_t m, int64_t n, int64_t k, const void *dC, int64_t lddc,
+                  const void *B, int64_t ldb, void *dA, int64_t ldda, void *stream_v) {
+    if (m < 0 || n < 0 || k < 0)
+        return set_error(TSM2_ERR_INVALID_VALUE, "%s: negative dimension (m=%lld n=%lld k=%lld)", fn, (long long)m,
+                         (long long)n, (long long)k);
+    if (lddc < (m > 1 ? m : 1))
+        return set_error(TSM2_ERR_INVALID_VALUE, "%s: lddc=%lld < max(1,m)", fn, (long long)lddc);
+    if (ldb < (n > 1 ? n : 1)) return set_error(TSM2_ERR_INVALID_VALUE, "%s: ldb=%lld < max(1,n)", fn, (long long)ldb);
+    if (ldda < (m > 1 ? m : 1))
+        return set_error(TSM2_ERR_INVALID_VALUE, "%s: ldda=%lld < max(1,m)", fn, (long long)ldda);
+    if (m > 0 && n > 0 && dA == nullptr) return set_error(TSM2_ERR_INVALID_VALUE, "%s: dA is NULL", fn);
+    if (m > 0 && n > 0 && k > 0 && (dC == nullptr || B == nullptr))
+        return set_error(TSM2_ERR_INVALID_VALUE, "%s: dC or B is NULL", fn);
+    if (m > 0 && n > 0 && k > 0) {
+        const size_t ob = span_bytes(m, n, ldda, elem);
+        if (ranges_overlap(dA, ob, dC, span_bytes(m, k, lddc, elem)) ||
+            ranges_overlap(dA, ob, B, span_bytes(n, k, ldb, elem)))
+            return set_error(TSM2_ERR_INVALID_VALUE, "%s: dA overlaps dC or B", fn);
+    }
+    if (m == 0 || n == 0) {
+        t_last_config = "empty";
+        return TSM2_SUCCESS;
+    }
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    if (k == 0) {
+        t_last_config = "zero-fill";
+        cudaError_t e = cudaMemset2DAsync(dA, (size_t)ldda * elem, 0, (size_t)m * elem, (size_t)n, stream);
+        return e == cudaSuccess ? TSM2_SUCCESS : cuda_error(e, "cudaMemset2DAsync");
+    }
+    DeviceState *dev = nullptr;
+    tsm2_status st = device_state(&dev);
+    if (st != TSM2_SUCCESS) return st;
+    const bool vec_ok = aligned16(dA) && (ldda * elem) % 16 == 0;
+    t_last_config = elem == 8 ? "rankk_f64" : "rankk_f32";
+    for (int64_t c0 = 0; c0 < k; c0 += 16) {
+        const int kk = (int)((k - c0) < 16 ? (k - c0) : 16);
+        cudaError_t e = rankk_launch(elem, m, n, kk, static_cast<const char *>(dC) + (size_t)c0 * lddc * elem, lddc,
+                                     static_cast<const char *>(B) + (size_t)c0 * ldb * elem, ldb, dA, ldda, vec_ok,
+                                     c0 > 0, dev->sm_count, stream);
+        if (e != cudaSuccess) return cuda_error(e, "rank-k kernel launch");
+    }
+    return TSM2_SUCCESS;
+}
+
 // ---- allocation-free variant of the binary32 TSM2R bulk-copy path -----------
 //
 // Some callers cannot call cudaMalloc at all: a process whose device memory is
@@ -485,6 +616,26 @@ void tsm2_shutdown(void) {
     }
     g_ws.clear();
     cudaSetDevice(cur);
+}
+
+tsm2_status tsm2r_t_d(int64_t m, int64_t n, int64_t k, const double *A, int64_t lda, const double *dC, int64_t lddc,
+                      double *dB, int64_t lddb, void *stream) {
+    return gemm_t("tsm2r_t_d", 8, m, n, k, A, lda, dC, lddc, dB, lddb, stream);
+}
+
+tsm2_status tsm2r_t_s(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *dC, int64_t lddc,
+                      float *dB, int64_t lddb, void *stream) {
+    return gemm_t("tsm2r_t_s", 4, m, n, k, A, lda, dC, lddc, dB, lddb, stream);
+}
+
+tsm2_status tsm2_rankk_d(int64_t m, int64_t n, int64_t k, const double *dC, int64_t lddc, const double *B, int64_t ldb,
+                         double *dA, int64_t ldda, void *stream) {
+    return rankk("tsm2_rankk_d", 8, m, n, k, dC, lddc, B, ldb, dA, ldda, stream);
+}
+
+tsm2_status tsm2_rankk_s(int64_t m, int64_t n, int64_t k, const float *dC, int64_t lddc, const float *B, int64_t ldb,
+                         float *dA, int64_t ldda, void *stream) {
+    return rankk("tsm2_rankk_s", 4, m, n, k, dC, lddc, B, ldb, dA, ldda, stream);
 }
 
 void tsm2_set_wait_budget_ns(int64_t ns) { g_wait_ns = ns < 0 ? 0 : ns; }
