@@ -422,6 +422,68 @@ def run_gpu(args):
                    "fwd_bwd_over_fwd": round(tot / times["fwd"], 3)}
         del A, B, dC, C, dB, dA
 
+    # ---- mixed precision: A in binary32, bfloat16, bfloat16 hi+lo (32768^2, k = 16) -----------
+    mixed = None
+    if not args.no_mixed:
+        import numpy as np
+
+        import oracle
+        m = n = 32768
+        k = 16
+        X = torch.empty((n, m), dtype=torch.float32, device=dev).t()
+        pkg.check(lib.tsm2_fill_logmag_s(m, n, 0, ti.MID_A, X.data_ptr(), m, sh))
+        Bm = torch.empty((k, n), dtype=torch.float32, device=dev).t()
+        pkg.check(lib.tsm2_fill_uniform_s(n, k, 0, ti.MID_B, Bm.data_ptr(), n, sh))
+        hi = torch.empty((n, m), dtype=torch.int16, device=dev)
+        lo = torch.empty((n, m), dtype=torch.int16, device=dev)
+        pkg.check(pkg.tsm2_split_bf16(m, n, X.data_ptr(), m, hi.data_ptr(), lo.data_ptr(), m, sh))
+        Cm = torch.empty((k, m), dtype=torch.float32, device=dev).t()
+        variants = {
+            "fp32": (lambda: pkg.tsm2r_s(m, n, k, X.data_ptr(), m, Bm.data_ptr(), n, Cm.data_ptr(), m, sh),
+                     4 * m * n + 4 * n * k + 4 * m * k),
+            "bf16": (lambda: pkg.tsm2r_bf16(m, n, k, hi.data_ptr(), None, m, Bm.data_ptr(), n, Cm.data_ptr(), m, sh),
+                     2 * m * n + 4 * n * k + 4 * m * k),
+            "bf16_hilo": (lambda: pkg.tsm2r_bf16(m, n, k, hi.data_ptr(), lo.data_ptr(), m, Bm.data_ptr(), n,
+                                                 Cm.data_ptr(), m, sh),
+                          4 * m * n + 4 * n * k + 4 * m * k),
+        }
+        rows = np.linspace(0, m - 1, 24).astype(np.int64)
+        Xr = ti.logmag(0, ti.MID_A, m, n, np.float32, row_idx=rows).astype(np.float64)
+        Bh = ti.uniform_pm1(0, ti.MID_B, n, k, np.float32).astype(np.float64)
+        ref = oracle.gemm(np.asfortranarray(Xr), Bh)
+        S = oracle.absgemm(np.asfortranarray(Xr), Bh)
+        mixed = {"workload": "32768 x 32768 A, magnitudes log-uniform over [2^-10, 2^10), random sign; "
+                             "B 32768 x 16 uniform[-1,1); error vs binary64 oracle on 24 sampled rows",
+                 "variants": {}}
+        for name, (f, nbytes) in variants.items():
+            ts = []
+            for r in range(args.warmup + max(3, min(args.steps, 10))):
+                l2_flush()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pkg.check(f())
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if r >= args.warmup:
+                    ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            cfgname = pkg.tsm2_last_config()
+            got = Cm.cpu().numpy()[rows].astype(np.float64)
+            err = np.abs(got - ref)
+            big = np.abs(ref) > 1e-6 * S
+            mixed["variants"][name] = {
+                "config": cfgname, "ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                "frac_hbm": round(nbytes / (ms * 1e-3) / 1e9 / peak_hbm, 3),
+                "max_err_over_absAB": float(f"{float(np.max(err / S)):.3e}"),
+                "normwise_rel_err": float(f"{float(np.linalg.norm(got - ref) / np.linalg.norm(ref)):.3e}"),
+                "max_rel_err": float(f"{float(np.max(err[big] / np.abs(ref[big]))):.3e}")}
+        pkg.check(pkg.tsm2_get_device_status(sh))
+        f32ms = mixed["variants"]["fp32"]["ms"]
+        for v in mixed["variants"].values():
+            v["speedup_vs_fp32"] = round(f32ms / v["ms"], 3)
+        del X, Bm, hi, lo, Cm
+        torch.cuda.empty_cache()
+
     # ---- end to end through the C ABI with host buffers --------------------------------------
     h_in, h_out = [], []
     for w in work32:
@@ -473,7 +535,8 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "step_wall_s": round(wall / args.steps, 4)},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
-        "clocks": clock_rec, "fp64": fp64, "fwd_bwd": fwd_bwd, "cases": case_rows, "src_hash": src_hash(),
+        "clocks": clock_rec, "fp64": fp64, "fwd_bwd": fwd_bwd, "mixed_precision": mixed, "cases": case_rows,
+        "src_hash": src_hash(),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -533,6 +596,7 @@ def main():
     ap.add_argument("--no-cublas", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fwdbwd", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--case", default=None, help="op:dtype:m:n:k, e.g. r:f32:8192:8192:16 -- time one multiply only")
     args = ap.parse_args()
     if args.case:

@@ -124,6 +124,29 @@ tsm2_status tsm2_rankk_d(int64_t m, int64_t n, int64_t k, const double *dC, int6
 tsm2_status tsm2_rankk_s(int64_t m, int64_t n, int64_t k, const float *dC, int64_t lddc,
                          const float *B, int64_t ldb, float *dA, int64_t ldda, void *stream);
 
+/* ---- bfloat16 storage of A (tensor cores) ---------------------------------- */
+
+/* TSM2R with A stored in bfloat16: C(m x k, binary32) = A B, B n x k binary32,
+ * binary32 accumulation.  A_hi holds bfloat16 bit patterns (column-major, lda),
+ * A_lo (same layout and lda) the optional low parts of a hi + lo split (see
+ * tsm2_split_bf16); NULL means A = A_hi.  The paper omits half precision
+ * (Sec. 4.1); this extends TSM2R (Sec. 3.1): A is streamed once, at half the
+ * bytes of binary32 (or the same bytes, with about 16 significant bits, for
+ * hi + lo), and the products run on the tensor cores (B is split exactly into
+ * three bfloat16 pieces internally).  Error: |C - A_hi B| <= about
+ * (2^-18 + 2 n 2^-23) |A_hi||B| (plain), |C - (A_hi + A_lo) B| <= about
+ * (2^-27 + 5 n 2^-23) |A||B| (hi + lo).  The bulk-copy path needs 16-byte
+ * aligned A_hi/A_lo and lda a multiple of 8; otherwise an element-wise
+ * CUDA-core path runs.  Uses the workspace (B pieces and split partial sums).
+ * Same error contract as tsm2r_s. */
+tsm2_status tsm2r_bf16(int64_t m, int64_t n, int64_t k, const uint16_t *A_hi, const uint16_t *A_lo,
+                       int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc, void *stream);
+
+/* hi = RNE_bf16(X), lo = RNE_bf16(X - hi) elementwise (X - hi is exact in
+ * binary32), rows x cols column-major; lo may be NULL.  hi and lo share ldh. */
+tsm2_status tsm2_split_bf16(int64_t rows, int64_t cols, const float *X, int64_t ldx,
+                            uint16_t *hi, uint16_t *lo, int64_t ldh, void *stream);
+
 /* TSM2R, binary32, allocating nothing.  The paper has no counterpart: this
  * is a library convenience.  Same arguments, result and error contract as
  * tsm2r_s, for callers that cannot call cudaMalloc at all -- a process whose

@@ -56,6 +56,10 @@ def _load():
                 f = getattr(lib, name)
                 f.argtypes = gemm_sig
                 f.restype = ctypes.c_int
+            lib.tsm2r_bf16.argtypes = [i64, i64, i64, vp, vp, i64, vp, i64, vp, i64, vp]
+            lib.tsm2r_bf16.restype = ctypes.c_int
+            lib.tsm2_split_bf16.argtypes = [i64, i64, vp, i64, vp, vp, i64, vp]
+            lib.tsm2_split_bf16.restype = ctypes.c_int
             lib.tsm2_get_last_error_string.restype = ctypes.c_char_p
             lib.tsm2_last_config.restype = ctypes.c_char_p
             lib.tsm2_get_device_status.argtypes = [vp]
@@ -120,6 +124,14 @@ def tsm2_rankk_d(m, n, k, dC, lddc, B, ldb, dA, ldda, stream=0):
 
 def tsm2_rankk_s(m, n, k, dC, lddc, B, ldb, dA, ldda, stream=0):
     return _load().tsm2_rankk_s(m, n, k, dC, lddc, B, ldb, dA, ldda, stream)
+
+
+def tsm2r_bf16(m, n, k, A_hi, A_lo, lda, B, ldb, C, ldc, stream=0):
+    return _load().tsm2r_bf16(m, n, k, A_hi, A_lo, lda, B, ldb, C, ldc, stream)
+
+
+def tsm2_split_bf16(rows, cols, X, ldx, hi, lo, ldh, stream=0):
+    return _load().tsm2_split_bf16(rows, cols, X, ldx, hi, lo, ldh, stream)
 
 
 def tsm2_get_last_error_string() -> str:
@@ -253,5 +265,5 @@ __all__ = [
     "tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s", "tsm2r_s_noalloc", "tsm2_get_last_error_string", "tsm2_last_config",
     "tsm2_get_device_status", "tsm2_shutdown", "tsm2_set_wait_budget_ns", "tsm2_set_path", "tsm2_set_grid", "tsm2_set_trace",
     "check", "tsm2r", "tsm2l", "tsm2r_t", "rankk", "empty_colmajor", "TSM2Error", "lib", "LIB_PATH",
-    "tsm2r_t_d", "tsm2r_t_s", "tsm2_rankk_d", "tsm2_rankk_s",
+    "tsm2r_t_d", "tsm2r_t_s", "tsm2_rankk_d", "tsm2_rankk_s", "tsm2r_bf16", "tsm2_split_bf16",
 ]

@@ -87,6 +87,33 @@ cudaError_t rankk_launch(int elem, int64_t m, int64_t n, int k, const void *dC, 
                          int64_t ldb, void *dA, int64_t ldda, bool vec_ok, bool accumulate, int sm_count,
                          cudaStream_t stream);
 
+// ---- bfloat16 A on the tensor cores (tsm2_bf16.cu) --------------------------
+
+struct BF16Launch {
+    int64_t m, n;
+    int k;               // <= 16
+    CUtensorMap mapHi;   // A_hi: bf16 dims {m, n}, box {64, 64}, 128-byte swizzle
+    CUtensorMap mapLo;   // A_lo (when hilo)
+    bool hilo;
+    const void *bpieces; // prepared B pieces (bf16_prep_b)
+    void *C;
+    int64_t ldc;
+    void *ws;
+    int *counters;
+    unsigned *status;
+    int64_t wait_ns;
+    int grid;
+};
+int bf16_bm();
+int bf16_bk();
+size_t bf16_bpieces_bytes(int64_t n);
+cudaError_t bf16_prep_b(int64_t n, int k, const float *B, int64_t ldb, void *out, cudaStream_t stream);
+cudaError_t bf16_launch(const BF16Launch &L, cudaStream_t stream);
+cudaError_t bf16_simple_launch(int64_t m, int64_t n, int k, const void *A_hi, const void *A_lo, int64_t lda,
+                               const float *B, int64_t ldb, float *C, int64_t ldc, cudaStream_t stream);
+cudaError_t split_bf16_launch(int64_t rows, int64_t cols, const float *X, int64_t ldx, void *hi, void *lo,
+                              int64_t ldh, int sm_count, cudaStream_t stream);
+
 // Work partition of the persistent grid (shared by host sizing and kernels).
 struct Partition {
     int64_t num_rb;  // row blocks

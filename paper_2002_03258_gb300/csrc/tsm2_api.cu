@@ -136,6 +136,21 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
+tsm2_status encode_2d_ex(CUtensorMap *map, CUtensorMapDataType dtype, int elem, const void *base, int64_t rows,
+                         int64_t cols, int64_t ld, int box_rows, int box_cols, CUtensorMapSwizzle swizzle) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return set_error(TSM2_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
+    const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * elem)};
+    const cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(map, dtype, 2, const_cast<void *>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(TSM2_ERR_CUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+    return TSM2_SUCCESS;
+}
+
 tsm2_status encode_2d(CUtensorMap *map, int elem, const void *base, int64_t rows, int64_t cols, int64_t ld,
                       int box_rows, int box_cols) {
     EncodeTiledFn fn = encode_fn();
@@ -420,6 +435,98 @@ tsm2_status rankk(const char *fn, int elem, int64_t m, int64_t n, int64_t k, con
     return TSM2_SUCCESS;
 }
 
+// ---- bfloat16 A (tensor cores) -------------------------------------------------
+
+tsm2_status gemm_bf16(int64_t m, int64_t n, int64_t k, const void *A_hi, const void *A_lo, int64_t lda,
+                      const float *B, int64_t ldb, float *C, int64_t ldc, void *stream_v) {
+    const char *fn = "tsm2r_bf16";
+    if (m < 0 || n < 0 || k < 0)
+        return set_error(TSM2_ERR_INVALID_VALUE, "%s: negative dimension (m=%lld n=%lld k=%lld)", fn, (long long)m,
+                         (long long)n, (long long)k);
+    if (lda < (m > 1 ? m : 1)) return set_error(TSM2_ERR_INVALID_VALUE, "%s: lda=%lld < max(1,m)", fn, (long long)lda);
+    if (ldb < (n > 1 ? n : 1)) return set_error(TSM2_ERR_INVALID_VALUE, "%s: ldb=%lld < max(1,n)", fn, (long long)ldb);
+    if (ldc < (m > 1 ? m : 1)) return set_error(TSM2_ERR_INVALID_VALUE, "%s: ldc=%lld < max(1,m)", fn, (long long)ldc);
+    if (m > 0 && k > 0 && C == nullptr) return set_error(TSM2_ERR_INVALID_VALUE, "%s: C is NULL", fn);
+    if (m > 0 && n > 0 && k > 0 && (A_hi == nullptr || B == nullptr))
+        return set_error(TSM2_ERR_INVALID_VALUE, "%s: A_hi or B is NULL", fn);
+    if (m > 0 && n > 0 && k > 0) {
+        const size_t cb = span_bytes(m, k, ldc, 4);
+        const size_t ab = span_bytes(m, n, lda, 2);
+        if (ranges_overlap(C, cb, A_hi, ab) || ranges_overlap(C, cb, A_lo, ab) ||
+            ranges_overlap(C, cb, B, span_bytes(n, k, ldb, 4)))
+            return set_error(TSM2_ERR_INVALID_VALUE, "%s: C overlaps A_hi, A_lo or B", fn);
+    }
+    if (m == 0 || k == 0) {
+        t_last_config = "empty";
+        return TSM2_SUCCESS;
+    }
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    if (n == 0) {
+        t_last_config = "zero-fill";
+        cudaError_t e = cudaMemset2DAsync(C, (size_t)ldc * 4, 0, (size_t)m * 4, (size_t)k, stream);
+        return e == cudaSuccess ? TSM2_SUCCESS : cuda_error(e, "cudaMemset2DAsync");
+    }
+    DeviceState *dev = nullptr;
+    tsm2_status st = device_state(&dev);
+    if (st != TSM2_SUCCESS) return st;
+    const bool ok = g_path != 1 && aligned16(A_hi) && (A_lo == nullptr || aligned16(A_lo)) && (lda * 2) % 16 == 0 &&
+                    m < (1ll << 31) - 4096 && n < (1ll << 31);
+    for (int64_t c0 = 0; c0 < k; c0 += 16) {
+        const int kk = (int)((k - c0) < 16 ? (k - c0) : 16);
+        const float *Bc = B + c0 * ldb;
+        float *Cc = C + c0 * ldc;
+        cudaError_t e;
+        if (!ok) {
+            t_last_config = "simple_bf16";
+            e = bf16_simple_launch(m, n, kk, A_hi, A_lo, lda, Bc, ldb, Cc, ldc, stream);
+            if (e != cudaSuccess) return cuda_error(e, "bf16 element-wise kernel launch");
+            continue;
+        }
+        BF16Launch L;
+        std::memset(&L, 0, sizeof L);
+        L.m = m;
+        L.n = n;
+        L.k = kk;
+        L.hilo = A_lo != nullptr;
+        st = encode_2d_ex(&L.mapHi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A_hi, m, n, lda, 64, bf16_bk(),
+                          CU_TENSOR_MAP_SWIZZLE_128B);
+        if (st != TSM2_SUCCESS) return st;
+        if (L.hilo) {
+            st = encode_2d_ex(&L.mapLo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A_lo, m, n, lda, 64, bf16_bk(),
+                              CU_TENSOR_MAP_SWIZZLE_128B);
+            if (st != TSM2_SUCCESS) return st;
+        }
+        const int64_t num_rb = (m + bf16_bm() - 1) / bf16_bm();
+        const int64_t upr = (n + bf16_bk() - 1) / bf16_bk();
+        const int64_t ngroups = num_rb * upr;
+        int64_t grid = dev->sm_count;
+        if (ngroups / 4 < grid) grid = ngroups / 4;
+        if (g_grid_override > 0) grid = g_grid_override;
+        if (grid > ngroups) grid = ngroups;
+        if (grid < 1) grid = 1;
+        const size_t pieces = (bf16_bpieces_bytes(n) + 255) / 256 * 256;
+        const size_t slots = (size_t)(grid + num_rb) * 16 * bf16_bm() * 4;
+        void *ws = nullptr;
+        int *counters = nullptr;
+        st = workspace(stream, (size_t)num_rb * sizeof(int), pieces + slots, &ws, &counters);
+        if (st != TSM2_SUCCESS) return st;
+        e = bf16_prep_b(n, kk, Bc, ldb, ws, stream);
+        if (e != cudaSuccess) return cuda_error(e, "bf16 B split kernel launch");
+        L.bpieces = ws;
+        L.ws = static_cast<char *>(ws) + pieces;
+        L.counters = counters;
+        L.C = Cc;
+        L.ldc = ldc;
+        L.status = dev->status;
+        L.wait_ns = g_wait_ns;
+        L.grid = (int)grid;
+        t_last_config = L.hilo ? "tc_bf16_hilo" : "tc_bf16";
+        e = bf16_launch(L, stream);
+        if (e != cudaSuccess) return cuda_error(e, "bf16 tensor-core kernel launch");
+    }
+    return TSM2_SUCCESS;
+}
+
 // ---- allocation-free variant of the binary32 TSM2R bulk-copy path -----------
 //
 // Some callers cannot call cudaMalloc at all: a process whose device memory is
@@ -636,6 +743,25 @@ tsm2_status tsm2_rankk_d(int64_t m, int64_t n, int64_t k, const double *dC, int6
 tsm2_status tsm2_rankk_s(int64_t m, int64_t n, int64_t k, const float *dC, int64_t lddc, const float *B, int64_t ldb,
                          float *dA, int64_t ldda, void *stream) {
     return rankk("tsm2_rankk_s", 4, m, n, k, dC, lddc, B, ldb, dA, ldda, stream);
+}
+
+tsm2_status tsm2r_bf16(int64_t m, int64_t n, int64_t k, const uint16_t *A_hi, const uint16_t *A_lo, int64_t lda,
+                       const float *B, int64_t ldb, float *C, int64_t ldc, void *stream) {
+    return gemm_bf16(m, n, k, A_hi, A_lo, lda, B, ldb, C, ldc, stream);
+}
+
+tsm2_status tsm2_split_bf16(int64_t rows, int64_t cols, const float *X, int64_t ldx, uint16_t *hi, uint16_t *lo,
+                            int64_t ldh, void *stream) {
+    if (rows < 0 || cols < 0) return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_split_bf16: negative dimension");
+    if (ldx < (rows > 1 ? rows : 1) || ldh < (rows > 1 ? rows : 1))
+        return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_split_bf16: leading dimension < max(1,rows)");
+    if (rows == 0 || cols == 0) return TSM2_SUCCESS;
+    if (!X || !hi) return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_split_bf16: X or hi is NULL");
+    DeviceState *dev = nullptr;
+    tsm2_status st = device_state(&dev);
+    if (st != TSM2_SUCCESS) return st;
+    cudaError_t e = split_bf16_launch(rows, cols, X, ldx, hi, lo, ldh, dev->sm_count, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? TSM2_SUCCESS : cuda_error(e, "split kernel launch");
 }
 
 void tsm2_set_wait_budget_ns(int64_t ns) { g_wait_ns = ns < 0 ? 0 : ns; }

@@ -1,0 +1,551 @@
+// TSM2R with A stored in bfloat16 (optionally as a hi + lo pair), B and C in
+// binary32, binary32 accumulation -- on the tensor cores (tcgen05 + TMEM).
+//
+// The contraction C(m x k) = A(m x n) B(n x k) is the paper's TSM2R (Sec. 3.1)
+// with A read once; with A in bfloat16 the FMA work per byte of A doubles,
+// which the CUDA cores cannot sustain at HBM speed, so the products run on
+// the tensor cores instead:
+//
+//  * B (binary32) is split exactly into three bfloat16 pieces, B = B1 + B2 + B3
+//    (each piece the round-to-nearest-even of the remainder), by a small prep
+//    kernel that also lays them out pre-tiled in the canonical K-major
+//    no-swizzle layout of the MMA B operand (8 x 16-byte core matrices).
+//  * A tiles (512 rows x 32 inner columns per stage, eight 64-row boxes, so
+//    DRAM sees 1 KB runs per column) arrive by TMA with the 128-byte swizzle,
+//    i.e. in the canonical MN-major SW128 layout of the MMA A operand (A is
+//    column-major, rows contiguous); each stage is four M = 128 row tiles.
+//  * One thread issues tcgen05.mma.kind::f16 (M = 128, N = 16, K = 16,
+//    bf16 x bf16 -> f32) into a TMEM accumulator:
+//        plain:  C += A * B1 + A * B2              (B to 16 bits: below the
+//                                                   2^-9 representation error of A)
+//        hi+lo:  C += Ahi*(B1+B2+B3) + Alo*(B1+B2) (drops only Alo*B3,
+//                                                   < 2^-26 |A||B| per product)
+//    tcgen05.commit releases each shared-memory stage back to the producer.
+//  * Each stage's MMAs accumulate into one of four TMEM buffers (4 x 64
+//    columns: 16 per row tile, so the MMAs can run stages ahead of the drain); four epilogue warps drain it with tcgen05.ld after every stage
+//    (one TMEM lane = one row of C) and carry the sum over stages in
+//    registers with round-to-nearest binary32 adds -- the tensor cores' own
+//    accumulation is then used for 4 (plain) or 20 (hi+lo) products' worth of
+//    partial sums only, which keeps hi+lo at binary32-like accuracy.  Pieces
+//    end in C, or in a partial sum for the same deterministic stream-K fix-up
+//    as the CUDA-core kernels.
+// Every wait is bounded; TMEM is always released before the block exits.
+#include "common.cuh"
+#include "internal.h"
+
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+namespace tsm2 {
+namespace {
+
+constexpr int kMM = 128;          // MMA M = TMEM lanes
+constexpr int kSub = 4;           // MMA row tiles per unit
+constexpr int kBM = kSub * kMM;   // 512 rows per unit: 1 KB contiguous per column of A
+constexpr int kKC = 16;           // C columns = MMA N
+constexpr int kBK = 32;           // inner columns per stage
+constexpr int kKSteps = kBK / 16; // MMA K steps per stage
+constexpr int kMaxStages = 8;     // stages are sized at run time: 6 (plain) or 3 (hi+lo)
+constexpr int kPieces = 3;        // bfloat16 pieces of B
+constexpr int kBox = 64 * kBK * 2;                     // one 64-row TMA box: 4 KB
+constexpr int kATile = kBM * kBK * 2;                  // 32 KB per A tile (8 boxes)
+constexpr int kBBlock = kPieces * kKSteps * 512;       // 3 KB of B pieces per stage
+constexpr int kStageHiLo = 2 * kATile + kBBlock;       // 67 KB
+constexpr int kStagePlain = kATile + kBBlock;          // 35 KB
+constexpr int kNBuf = 4;                               // TMEM accumulator buffers
+constexpr int kBufCols = kSub * kKC;                   // 64 columns per buffer
+constexpr int kTmemCols = kNBuf * kBufCols;            // 256 columns
+constexpr int kSmemBudget = 210 * 1024;                // ring bytes (barriers follow)
+static_assert(kSmemBudget / kStageHiLo >= 3 && kSmemBudget + 1024 + 512 <= 227 * 1024, "shared memory budget");
+static_assert(kStageHiLo % 1024 == 0 && kStagePlain % 1024 == 0 && kBox % 1024 == 0, "1 KB alignment of A boxes");
+
+// Instruction descriptor, kind::f16: D f32, A bf16, B bf16, A MN-major
+// (column-major A: rows contiguous), B K-major, N = 16, M = 128.
+constexpr uint32_t kIdesc = (1u << 4)          // D format f32
+                            | (1u << 7)        // A format bf16
+                            | (1u << 10)       // B format bf16
+                            | (1u << 15)       // A major: MN
+                            | (0u << 16)       // B major: K
+                            | ((kKC >> 3) << 17)
+                            | ((kMM >> 4) << 24);
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading and
+// stride byte offsets (all >> 4), fixed version 1 (bits 46-47), layout type
+// (bits 61-63: 0 = no swizzle, 2 = 128-byte swizzle).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)(layout & 7u) << 61;
+    return d;
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+struct BParams {
+    int64_t m, n;
+    int k;
+    const unsigned char *bpieces;  // [n/BK blocks][piece][kstep][512 B], device
+    float *C;
+    int64_t ldc;
+    float *ws;
+    int *counters;
+    unsigned *status;
+    int64_t wait_ns;
+    int64_t upr;     // stages per row block
+    int64_t ngroups; // units in total
+    int hilo;
+    int stages;       // ring depth
+    int stage_bytes;  // ring stride (A_hi, [A_lo], B pieces)
+};
+
+__device__ __forceinline__ int64_t owner_b(int64_t x, int64_t G, int64_t NG) { return ((x + 1) * G + NG - 1) / NG - 1; }
+
+__global__ void __launch_bounds__(192, 1)
+bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ CUtensorMap mapLo, const BParams p) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kSmemBudget);
+    uint64_t *full = bars;                   // [stages] TMA landed
+    uint64_t *empty = bars + kMaxStages;     // [stages] MMAs done with the stage
+    uint64_t *accf = bars + 2 * kMaxStages;  // [kNBuf] stage sum complete in TMEM
+    uint64_t *acce = accf + kNBuf;           // [kNBuf] drained by the epilogue
+    uint64_t *fin = acce + kNBuf;            // [1] all MMAs finished
+    const int nst = p.stages;
+    const int sbytes = p.stage_bytes;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
+    volatile int *flags = reinterpret_cast<volatile int *>(tmem_slot + 2);  // [0] abort, [1] last
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t G = gridDim.x, g = blockIdx.x;
+    const int64_t u_begin = g * p.ngroups / G;
+    const int64_t u_end = (g + 1) * p.ngroups / G;
+    const int nunits = (int)(u_end - u_begin);
+    const int upr = (int)p.upr;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < nst; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < kNBuf; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 4);
+        }
+        mbar_init(fin, 1);
+        flags[0] = 0;
+        flags[1] = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(tmem_slot);
+
+    if (warp == 0) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            prefetch_tensormap(&mapHi);
+            if (p.hilo) prefetch_tensormap(&mapLo);
+            const uint64_t policy = l2_policy_evict_first();
+            const uint32_t tx = (uint32_t)((p.hilo ? 2 : 1) * kATile + kBBlock);
+            int s = 0;
+            uint32_t ph = 0, issued = 0, last_par = 0;
+            int rb = (int)(u_begin / p.upr);
+            int kc = (int)(u_begin - (int64_t)rb * p.upr);
+            for (int i = 0; i < nunits; ++i) {
+                if (flags[0]) break;
+                if (!mbar_wait_bounded(&empty[s], ph ^ 1u, p.wait_ns, flags)) {
+                    flags[0] = 1;
+                    atomicOr(p.status, kStatusTimeout);
+                    break;
+                }
+                unsigned char *st = smem + s * sbytes;
+                mbar_arrive_expect_tx(&full[s], tx);
+                const int32_t x0 = rb * kBM, y0 = kc * kBK;
+#pragma unroll
+                for (int q = 0; q < kBM / 64; ++q) {
+                    tma_load_2d_hint(st + q * kBox, &mapHi, x0 + q * 64, y0, &full[s], policy);
+                    if (p.hilo) tma_load_2d_hint(st + kATile + q * kBox, &mapLo, x0 + q * 64, y0, &full[s], policy);
+                }
+                bulk_g2s(st + sbytes - kBBlock, p.bpieces + (size_t)kc * kBBlock, kBBlock, &full[s]);
+                issued |= 1u << s;
+                last_par = (last_par & ~(1u << s)) | (ph << s);
+                if (++s == nst) { s = 0; ph ^= 1u; }
+                if (++kc == upr) { kc = 0; ++rb; }
+            }
+            for (int t = 0; t < nst; ++t)
+                if (issued & (1u << t)) (void)mbar_wait_bounded(&full[t], (last_par >> t) & 1u, 4000000000LL, nullptr);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            uint32_t acc_ph = 0;  // bit b: parity of buffer b
+            int buf = 0;
+            bool issued_any = false;
+            for (int i = 0; i < nunits; ++i) {
+                if (flags[0]) break;
+                // Each stage accumulates into its own TMEM buffer, which the
+                // epilogue must have drained (two buffers alternate).
+                if (!mbar_wait_bounded(&acce[buf], ((acc_ph >> buf) & 1u) ^ 1u, p.wait_ns, flags)) {
+                    flags[0] = 1;
+                    atomicOr(p.status, kStatusTimeout);
+                    break;
+                }
+                if (!mbar_wait_bounded(&full[s], ph, p.wait_ns, flags)) {
+                    flags[0] = 1;
+                    atomicOr(p.status, kStatusTimeout);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st = smem_u32(smem + s * sbytes);
+#pragma unroll
+                for (int ks = 0; ks < kKSteps; ++ks) {
+                    // B pieces: K-major, no swizzle: K-halves 128 B apart (LBO),
+                    // 8-column groups of C 256 B apart (SBO).
+                    const uint32_t bb = st + sbytes - kBBlock + ks * 512;
+                    const uint64_t b1 = sdesc(bb, 128, 256, 0);
+                    const uint64_t b2 = sdesc(bb + kKSteps * 512, 128, 256, 0);
+                    const uint64_t b3 = sdesc(bb + 2 * kKSteps * 512, 128, 256, 0);
+#pragma unroll
+                    for (int sub = 0; sub < kSub; ++sub) {
+                        // A row tile sub: MN-major SW128, its two 64-row boxes
+                        // 4 KB apart (LBO), 8-column groups 1 KB apart (SBO).
+                        const uint32_t aoff = sub * 2 * kBox + ks * 2048;
+                        const uint64_t ahi = sdesc(st + aoff, kBox, 1024, 2);
+                        const uint64_t alo = sdesc(st + kATile + aoff, kBox, 1024, 2);
+                        const uint32_t d = tmem + (uint32_t)(buf * kBufCols + sub * kKC);
+                        umma_f16(d, ahi, b1, ks == 0 ? 0u : 1u);
+                        umma_f16(d, ahi, b2, 1u);
+                        if (p.hilo) {
+                            umma_f16(d, ahi, b3, 1u);
+                            umma_f16(d, alo, b1, 1u);
+                            umma_f16(d, alo, b2, 1u);
+                        }
+                    }
+                }
+                issued_any = true;
+                umma_commit(&empty[s]);     // stage s may be refilled once these MMAs are done
+                umma_commit(&accf[buf]);    // and this stage's sum is ready for the epilogue
+                acc_ph ^= 1u << buf;
+                if (++buf == kNBuf) buf = 0;
+                if (++s == nst) { s = 0; ph ^= 1u; }
+            }
+            // Every MMA this thread issued has completed before TMEM is freed.
+            if (issued_any) {
+                umma_commit(fin);
+                (void)mbar_wait_bounded(fin, 0, 4000000000LL, nullptr);
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5, one TMEM lane quarter each ----------------
+        const int quarter = warp & 3;          // TMEM lanes 32*quarter .. +31
+        const int r = quarter * 32 + lane;     // row within each 128-row tile
+        const int et = threadIdx.x - 64;       // 0 .. 127
+        uint32_t acc_ph = 0;
+        int buf = 0;
+        bool aborted = false;
+        int rb = (int)(u_begin / p.upr);
+        int kc = (int)(u_begin - (int64_t)rb * p.upr);
+        bool piece_at_start = (kc == 0);
+        // The tensor cores sum 16-term products over one stage only; the long
+        // sum over stages runs here in binary32 with round-to-nearest adds.
+        float v[kSub][kKC];
+#pragma unroll
+        for (int sub = 0; sub < kSub; ++sub)
+#pragma unroll
+            for (int c = 0; c < kKC; ++c) v[sub][c] = 0.f;
+        for (int i = 0; i < nunits; ++i) {
+            const bool rb_end = (kc == upr - 1);
+            if (!aborted) {
+                bool ok = !flags[0] && mbar_wait_bounded(&accf[buf], (acc_ph >> buf) & 1u, p.wait_ns, flags);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) {
+                    aborted = true;
+                    if (lane == 0) {
+                        flags[0] = 1;
+                        atomicOr(p.status, kStatusTimeout);
+                    }
+                }
+            }
+            if (!aborted) {
+                tc_fence_after();
+#pragma unroll
+                for (int sub = 0; sub < kSub; ++sub) {
+                    float t[16];
+                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * kBufCols + sub * kKC), t);
+#pragma unroll
+                    for (int c = 0; c < kKC; ++c) v[sub][c] += t[c];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[buf]);
+            }
+            acc_ph ^= 1u << buf;
+            if (++buf == kNBuf) buf = 0;
+            if (rb_end || i == nunits - 1) {
+                const bool whole = piece_at_start && rb_end;
+                const int64_t rb64 = rb;
+                const int64_t row0 = rb64 * kBM;
+                if (whole) {
+                    if (!aborted)
+#pragma unroll
+                        for (int sub = 0; sub < kSub; ++sub) {
+                            const int64_t row = row0 + sub * kMM + r;
+                            if (row < p.m)
+#pragma unroll
+                                for (int c = 0; c < kKC; ++c)
+                                    if (c < p.k) p.C[row + (int64_t)c * p.ldc] = v[sub][c];
+                        }
+                } else {
+                    const int64_t rb_u0 = rb64 * p.upr;
+                    const int64_t gA = owner_b(rb_u0, G, p.ngroups);
+                    const int64_t gB = owner_b(rb_u0 + p.upr - 1, G, p.ngroups);
+                    float *slot = p.ws + (g + rb64) * (int64_t)(kKC * kBM);
+#pragma unroll
+                    for (int sub = 0; sub < kSub; ++sub)
+#pragma unroll
+                        for (int c = 0; c < kKC; ++c) __stcg(slot + c * kBM + sub * kMM + r, v[sub][c]);
+                    __threadfence();
+                    named_bar_sync(1, 128);
+                    if (et == 0) {
+                        int last = 0;
+                        if (!flags[0]) {
+                            const int old = atomicAdd(&p.counters[rb], 1);
+                            last = (old == (int)(gB - gA));
+                            if (last) p.counters[rb] = 0;
+                        }
+                        flags[1] = last;
+                    }
+                    named_bar_sync(1, 128);
+                    if (flags[1]) {
+                        __threadfence();
+#pragma unroll 1
+                        for (int sub = 0; sub < kSub; ++sub) {
+                            float sum[kKC];
+                            const float *src = p.ws + (gA + rb64) * (int64_t)(kKC * kBM) + sub * kMM + r;
+#pragma unroll
+                            for (int c = 0; c < kKC; ++c) sum[c] = __ldcg(src + c * kBM);
+                            for (int64_t gp = gA + 1; gp <= gB; ++gp) {
+                                src += kKC * kBM;
+                                float x[kKC];
+#pragma unroll
+                                for (int c = 0; c < kKC; ++c) x[c] = __ldcg(src + c * kBM);
+#pragma unroll
+                                for (int c = 0; c < kKC; ++c) sum[c] += x[c];
+                            }
+                            const int64_t row = row0 + sub * kMM + r;
+                            if (row < p.m)
+#pragma unroll
+                                for (int c = 0; c < kKC; ++c)
+                                    if (c < p.k) p.C[row + (int64_t)c * p.ldc] = sum[c];
+                        }
+                    }
+                    named_bar_sync(1, 128);  // flags[1] is reused by the next piece
+                }
+                piece_at_start = true;
+#pragma unroll
+                for (int sub = 0; sub < kSub; ++sub)
+#pragma unroll
+                    for (int c = 0; c < kKC; ++c) v[sub][c] = 0.f;
+            }
+            if (++kc == upr) { kc = 0; ++rb; }
+        }
+    }
+    // Everyone (including idle lanes) meets here before the TMEM is freed.
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// Split binary32 B (n x k, k <= 16) into three bfloat16 pieces, written in the
+// MMA B-operand layout [n/64 blocks][piece][kstep][core nb][core kb][8][8].
+__global__ void bsplit_kernel(int64_t n, int k, const float *__restrict__ B, int64_t ldb, __nv_bfloat16 *out,
+                              int64_t nblocks) {
+    const int64_t total = nblocks * kPieces * kKSteps * 256;  // bf16 elements
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t q = t;
+        const int e = (int)(q % 8); q /= 8;
+        const int rr = (int)(q % 8); q /= 8;
+        const int kb = (int)(q % 2); q /= 2;
+        const int nb = (int)(q % 2); q /= 2;
+        const int ks = (int)(q % kKSteps); q /= kKSteps;
+        const int piece = (int)(q % kPieces); q /= kPieces;
+        const int64_t blk = q;
+        const int64_t j = blk * kBK + ks * 16 + kb * 8 + e;
+        const int c = nb * 8 + rr;
+        const float b = (j < n && c < k) ? B[j + (int64_t)c * ldb] : 0.f;
+        const __nv_bfloat16 b1 = __float2bfloat16_rn(b);
+        const float r1 = b - __bfloat162float(b1);
+        const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(b2);
+        const __nv_bfloat16 b3 = __float2bfloat16_rn(r2);
+        out[t] = piece == 0 ? b1 : piece == 1 ? b2 : b3;
+    }
+}
+
+// Element-wise path (any alignment): one thread per row, bf16 -> f32 in
+// registers, binary32 FMAs with B.
+__global__ void __launch_bounds__(128) bf16_simple_kernel(int64_t m, int64_t n, int k, const __nv_bfloat16 *A_hi,
+                                                          const __nv_bfloat16 *A_lo, int64_t lda, const float *B,
+                                                          int64_t ldb, float *C, int64_t ldc) {
+    __shared__ float Bs[64][kKC];
+    const int64_t row = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    float acc[kKC];
+#pragma unroll
+    for (int c = 0; c < kKC; ++c) acc[c] = 0.f;
+    for (int64_t j0 = 0; j0 < n; j0 += 64) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < 64 * kKC; t += 128) {
+            const int jj = t % 64, c = t / 64;
+            Bs[jj][c] = (j0 + jj < n && c < k) ? B[j0 + jj + (int64_t)c * ldb] : 0.f;
+        }
+        __syncthreads();
+        if (row < m) {
+            const int jn = (int)((n - j0) < 64 ? (n - j0) : 64);
+            for (int jj = 0; jj < jn; ++jj) {
+                float a = __bfloat162float(A_hi[row + (j0 + jj) * lda]);
+                if (A_lo) a += __bfloat162float(A_lo[row + (j0 + jj) * lda]);  // exact: 16 significant bits
+#pragma unroll
+                for (int c = 0; c < kKC; ++c) acc[c] = fmaf(a, Bs[jj][c], acc[c]);
+            }
+        }
+    }
+    if (row < m)
+#pragma unroll
+        for (int c = 0; c < kKC; ++c)
+            if (c < k) C[row + (int64_t)c * ldc] = acc[c];
+}
+
+// x -> hi = RNE_bf16(x), lo = RNE_bf16(x - hi) (x - hi is exact in binary32).
+__global__ void split_kernel(int64_t rows, int64_t cols, const float *X, int64_t ldx, __nv_bfloat16 *hi,
+                             __nv_bfloat16 *lo, int64_t ldh) {
+    const int64_t total = rows * cols;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / rows, i = t - (t / rows) * rows;
+        const float x = X[i + j * ldx];
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        hi[i + j * ldh] = h;
+        if (lo) lo[i + j * ldh] = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+}
+
+}  // namespace
+
+int bf16_bm() { return kBM; }
+int bf16_bk() { return kBK; }
+size_t bf16_bpieces_bytes(int64_t n) { return (size_t)((n + kBK - 1) / kBK) * kBBlock; }
+
+cudaError_t bf16_prep_b(int64_t n, int k, const float *B, int64_t ldb, void *out, cudaStream_t stream) {
+    const int64_t nblocks = (n + kBK - 1) / kBK;
+    const int64_t total = nblocks * kPieces * kKSteps * 256;
+    int64_t grid = (total + 255) / 256;
+    if (grid > 4096) grid = 4096;
+    bsplit_kernel<<<(unsigned)grid, 256, 0, stream>>>(n, k, B, ldb, static_cast<__nv_bfloat16 *>(out), nblocks);
+    return cudaGetLastError();
+}
+
+cudaError_t bf16_launch(const BF16Launch &L, cudaStream_t stream) {
+    static std::mutex mu;
+    static uint64_t attr_done = 0;
+    const int smem = kSmemBudget + 1024 + 512;  // ring + 1 KB alignment slack + barriers
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < 64 && !(attr_done & (1ull << dev))) {
+            e = cudaFuncSetAttribute(bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            attr_done |= 1ull << dev;
+        }
+    }
+    BParams p;
+    p.m = L.m;
+    p.n = L.n;
+    p.k = L.k;
+    p.bpieces = static_cast<const unsigned char *>(L.bpieces);
+    p.C = static_cast<float *>(L.C);
+    p.ldc = L.ldc;
+    p.ws = static_cast<float *>(L.ws);
+    p.counters = L.counters;
+    p.status = L.status;
+    p.wait_ns = L.wait_ns;
+    p.upr = (L.n + kBK - 1) / kBK;
+    p.ngroups = ((L.m + kBM - 1) / kBM) * p.upr;
+    p.hilo = L.hilo ? 1 : 0;
+    p.stage_bytes = L.hilo ? kStageHiLo : kStagePlain;
+    p.stages = kSmemBudget / p.stage_bytes;
+    if (p.stages > kMaxStages) p.stages = kMaxStages;
+    bf16_kernel<<<L.grid, 192, smem, stream>>>(L.mapHi, L.mapLo, p);
+    return cudaGetLastError();
+}
+
+cudaError_t bf16_simple_launch(int64_t m, int64_t n, int k, const void *A_hi, const void *A_lo, int64_t lda,
+                               const float *B, int64_t ldb, float *C, int64_t ldc, cudaStream_t stream) {
+    if (m <= 0) return cudaSuccess;
+    bf16_simple_kernel<<<(unsigned)((m + 127) / 128), 128, 0, stream>>>(
+        m, n, k, static_cast<const __nv_bfloat16 *>(A_hi), static_cast<const __nv_bfloat16 *>(A_lo), lda, B, ldb, C,
+        ldc);
+    return cudaGetLastError();
+}
+
+cudaError_t split_bf16_launch(int64_t rows, int64_t cols, const float *X, int64_t ldx, void *hi, void *lo,
+                              int64_t ldh, int sm_count, cudaStream_t stream) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    const int64_t total = rows * cols;
+    int64_t grid = (total + 255) / 256;
+    if (grid > (int64_t)sm_count * 32) grid = (int64_t)sm_count * 32;
+    split_kernel<<<(unsigned)grid, 256, 0, stream>>>(rows, cols, X, ldx, static_cast<__nv_bfloat16 *>(hi),
+                                                    static_cast<__nv_bfloat16 *>(lo), ldh);
+    return cudaGetLastError();
+}
+
+}  // namespace tsm2
