@@ -484,6 +484,78 @@ def run_gpu(args):
         del X, Bm, hi, lo, Cm
         torch.cuda.empty_cache()
 
+    # ---- batched uneven problems: one graph launch vs a loop of plain launches ---------------
+    batched = None
+    if not args.no_batched:
+        import paper_2002_03258_gb300.batched as bt
+        from paper_2002_03258_gb300.autotune import autotune
+        shapes = ti.batch_shapes(0)
+        probs, keep, loop_calls = [], [], []
+        total = 0
+        for idx, (op, m, n, k) in enumerate(shapes):
+            lda = (m + 3) // 4 * 4
+            ldb = (n + 3) // 4 * 4
+            tA = torch.empty((n, lda), dtype=torch.float32, device=dev)
+            tB = torch.empty((k, ldb), dtype=torch.float32, device=dev)
+            tC = torch.empty((k, lda), dtype=torch.float32, device=dev)
+            pkg.check(lib.tsm2_fill_uniform_s(m, n, idx, ti.MID_A, tA.data_ptr(), lda, sh))
+            pkg.check(lib.tsm2_fill_uniform_s(n, k, idx, ti.MID_B, tB.data_ptr(), ldb, sh))
+            keep += [tA, tB, tC]
+            probs.append(bt.problem(op, m, n, k, tA.data_ptr(), lda, tB.data_ptr(), ldb, tC.data_ptr(), lda))
+            fn = pkg.tsm2r_s if op == "r" else pkg.tsm2l_s
+            loop_calls.append((fn, (m, n, k, tA.data_ptr(), lda, tB.data_ptr(), ldb, tC.data_ptr(), lda, sh)))
+            total += 4 * (m * n + n * k + m * k)
+        torch.cuda.synchronize()
+
+        def loop():
+            for fn, a in loop_calls:
+                pkg.check(fn(*a))
+
+        def timed(fn, reps):
+            ts = []
+            for _ in range(reps):
+                l2_flush()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return statistics.median(ts)
+
+        reps = max(3, min(args.steps, 5))
+        loop()
+        t_loop = timed(loop, reps)
+        plan0 = bt.BatchPlan(probs, 0)
+        plan0.graph_launch(sh)
+        t_default = timed(lambda: plan0.graph_launch(sh), reps)
+        classes0 = plan0.classes()
+        plan0.close()
+        tuned, rec = autotune(probs, reps=3, flush=l2_flush)
+        t_tuned = timed(lambda: tuned.graph_launch(sh), reps)
+        pkg.check(pkg.tsm2_get_device_status(sh))
+        batched = {
+            "workload": "512 problems: 256 TSM2R (n = m uniform in [512, 8192], k in {2..16}), 256 TSM2L "
+                        "(m in [2^14, 2^20], n = k in {4..32}), binary32 uniform[-1,1), seed 0",
+            "algorithmic_bytes": total,
+            "loop_of_plain_launches_ms": round(t_loop, 4),
+            "graph_default_shares_ms": round(t_default, 4),
+            "graph_autotuned_ms": round(t_tuned, 4),
+            "gbs": {"loop": round(total / (t_loop * 1e-3) / 1e9, 1),
+                    "graph_default": round(total / (t_default * 1e-3) / 1e9, 1),
+                    "graph_autotuned": round(total / (t_tuned * 1e-3) / 1e9, 1)},
+            "speedup_autotuned_vs_loop": round(t_loop / t_tuned, 3),
+            "autotuned": {"flags": rec["flags"], "grids": rec["grids"], "serial": rec["serial"],
+                          "classes": [c["name"] for c in tuned.classes()]},
+            "default_classes": [(c["name"], c["nprob"], c["grid"]) for c in classes0],
+            "trials": [(t["flags"], t["shares"], t["ms"]) for t in rec["trials"]],
+            "class_alone_ms": {str(t["flags"]): list(zip(t["classes"], t["class_alone_ms"]))
+                               for t in rec["trials"] if t["shares"] == "bytes"},
+        }
+        tuned.close()
+        del keep, probs, loop_calls
+        torch.cuda.empty_cache()
+
     # ---- end to end through the C ABI with host buffers --------------------------------------
     h_in, h_out = [], []
     for w in work32:
@@ -535,7 +607,8 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "step_wall_s": round(wall / args.steps, 4)},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
-        "clocks": clock_rec, "fp64": fp64, "fwd_bwd": fwd_bwd, "mixed_precision": mixed, "cases": case_rows,
+        "clocks": clock_rec, "fp64": fp64, "fwd_bwd": fwd_bwd, "mixed_precision": mixed, "batched": batched,
+        "cases": case_rows,
         "src_hash": src_hash(),
     }
     if rank == 0:
@@ -597,6 +670,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fwdbwd", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--case", default=None, help="op:dtype:m:n:k, e.g. r:f32:8192:8192:16 -- time one multiply only")
     args = ap.parse_args()
     if args.case:

@@ -174,6 +174,74 @@ tsm2_status tsm2r_s_noalloc(int64_t m, int64_t n, int64_t k,
                             const float *B, int64_t ldb,
                             float *C, int64_t ldc, void *stream);
 
+/* ---- Batches of uneven problems (binary32) ----------------------------------
+ *
+ * Many TSM2R / TSM2L problems of different shapes executed as one unit.  The
+ * problems are grouped into tile classes (schedule and C-column width); each
+ * class runs as ONE persistent kernel whose blocks each take an equal,
+ * contiguous share of the class's work units, crossing problem boundaries
+ * (Algorithm 5's persistent walk over tiles, Sec. 3.2.2, extended across
+ * problems).  The class kernels run concurrently on SM shares set by
+ * tsm2_batch_plan_set_grids (by default proportional to their bytes; the
+ * Python autotuner measures and sets them), and a whole batch can be replayed
+ * as one CUDA graph launch. */
+
+typedef struct tsm2_problem_s {
+    char op;             /* 'r' (TSM2R schedule) or 'l' (TSM2L: n, k <= 64) */
+    int64_t m, n, k;
+    const float *A;      /* m x n, column-major, lda; device */
+    int64_t lda;
+    const float *B;      /* n x k, ldb */
+    int64_t ldb;
+    float *C;            /* m x k, ldc; overwritten */
+    int64_t ldc;
+} tsm2_problem_s;
+
+typedef struct tsm2_batch_plan_s *tsm2_batch_plan_t;
+
+/* Plan flags (tile choices offered to the autotuner). */
+#define TSM2_BATCH_WIDE_L 1   /* TSM2L problems: 8 rows per lane (else 4) */
+#define TSM2_BATCH_MERGE_R 2  /* all TSM2R problems in one class (C columns padded to 16) */
+#define TSM2_BATCH_MERGE_L 4  /* all TSM2L problems in one class (padded to 32) */
+
+/* Validates the problems (argument rules of tsm2r_s; additionally every A,
+ * and B of TSM2R problems, must be 16-byte aligned with 16-byte multiple
+ * leading-dimension strides: TSM2_ERR_UNSUPPORTED otherwise), encodes their
+ * tensor maps and uploads the plan's tables and workspace (cudaMalloc: make
+ * plans outside timed or captured regions).  The operand pointers are
+ * recorded: the plan computes on whatever those buffers hold at execution.
+ * Problems with k > 16 (TSM2R) or k > 32 (TSM2L) are split into column
+ * groups.  *out receives the plan. */
+tsm2_status tsm2_batch_plan_create_s(int nprob, const tsm2_problem_s *probs, int flags,
+                                     tsm2_batch_plan_t *out);
+
+/* Runs every problem of the plan on `stream` (class kernels forked onto
+ * internal streams and joined back).  Plans must not run concurrently with
+ * themselves (their workspace is shared). */
+tsm2_status tsm2_batch_plan_execute(tsm2_batch_plan_t plan, void *stream);
+
+/* Runs only class `cls` on `stream`, on all SMs (used to measure classes). */
+tsm2_status tsm2_batch_plan_execute_class(tsm2_batch_plan_t plan, int cls, void *stream);
+
+/* Captures tsm2_batch_plan_execute once into a CUDA graph, on a stream the
+ * plan owns (re-captured after tsm2_batch_plan_set_grids), and launches the
+ * graph on `stream` (any stream, including the legacy default stream 0). */
+tsm2_status tsm2_batch_plan_graph_launch(tsm2_batch_plan_t plan, void *stream);
+
+int tsm2_batch_plan_num_classes(tsm2_batch_plan_t plan);
+tsm2_status tsm2_batch_plan_class_info(tsm2_batch_plan_t plan, int cls, const char **name, double *bytes,
+                                       int *grid, int *nprob);
+
+/* Sets the number of persistent blocks of every class (each in [1, #SMs]). */
+tsm2_status tsm2_batch_plan_set_grids(tsm2_batch_plan_t plan, int ncls, const int *grids);
+
+/* serial != 0: tsm2_batch_plan_execute runs the classes one after another on
+ * `stream`, each on all SMs (as tsm2_batch_plan_execute_class), instead of
+ * concurrently on their SM shares.  Default 0. */
+tsm2_status tsm2_batch_plan_set_serial(tsm2_batch_plan_t plan, int serial);
+
+void tsm2_batch_plan_destroy(tsm2_batch_plan_t plan);
+
 /* Message describing the last error returned to the calling host thread
  * (thread-local; valid until that thread's next call). Never NULL. */
 const char *tsm2_get_last_error_string(void);

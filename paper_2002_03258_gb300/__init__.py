@@ -60,6 +60,27 @@ def _load():
             lib.tsm2r_bf16.restype = ctypes.c_int
             lib.tsm2_split_bf16.argtypes = [i64, i64, vp, i64, vp, vp, i64, vp]
             lib.tsm2_split_bf16.restype = ctypes.c_int
+            i32 = ctypes.c_int
+            lib.tsm2_batch_plan_create_s.argtypes = [i32, vp, i32, ctypes.POINTER(vp)]
+            lib.tsm2_batch_plan_create_s.restype = i32
+            for name in ("tsm2_batch_plan_execute", "tsm2_batch_plan_graph_launch"):
+                f = getattr(lib, name)
+                f.argtypes = [vp, vp]
+                f.restype = i32
+            lib.tsm2_batch_plan_execute_class.argtypes = [vp, i32, vp]
+            lib.tsm2_batch_plan_execute_class.restype = i32
+            lib.tsm2_batch_plan_num_classes.argtypes = [vp]
+            lib.tsm2_batch_plan_num_classes.restype = i32
+            lib.tsm2_batch_plan_class_info.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_char_p),
+                                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32),
+                                                       ctypes.POINTER(i32)]
+            lib.tsm2_batch_plan_class_info.restype = i32
+            lib.tsm2_batch_plan_set_grids.argtypes = [vp, i32, ctypes.POINTER(i32)]
+            lib.tsm2_batch_plan_set_grids.restype = i32
+            lib.tsm2_batch_plan_set_serial.argtypes = [vp, i32]
+            lib.tsm2_batch_plan_set_serial.restype = i32
+            lib.tsm2_batch_plan_destroy.argtypes = [vp]
+            lib.tsm2_batch_plan_destroy.restype = None
             lib.tsm2_get_last_error_string.restype = ctypes.c_char_p
             lib.tsm2_last_config.restype = ctypes.c_char_p
             lib.tsm2_get_device_status.argtypes = [vp]

@@ -114,6 +114,37 @@ cudaError_t bf16_simple_launch(int64_t m, int64_t n, int k, const void *A_hi, co
 cudaError_t split_bf16_launch(int64_t rows, int64_t cols, const float *X, int64_t ldx, void *hi, void *lo,
                               int64_t ldh, int sm_count, cudaStream_t stream);
 
+// ---- batched problems (tsm2_batched.cu) --------------------------------------
+
+// Device-side descriptor of one problem of a batch class.
+struct alignas(64) ProbDesc {
+    CUtensorMap mapA;      // A: dims {m, n}, box {BOXM, BNS}
+    CUtensorMap mapB;      // B: dims {n, k}, box {BNS, KC} (TSM2R classes)
+    int64_t m, n, ldb, ldc;
+    const void *B;         // TSM2L classes: B is read with ordinary loads
+    void *C;
+    int64_t group_begin;   // first work group of the problem in the class numbering
+    int64_t rb_begin;      // first row block (counters and partial-sum slots)
+    int32_t k, upr, gran, c_vec;
+};
+struct BatchLaunch {
+    const ProbDesc *probs;
+    int nprob;
+    int64_t ngroups;
+    void *ws;
+    int *counters;
+    unsigned *status;
+    int64_t wait_ns;
+    int grid;
+};
+struct BatchClass {
+    char op;  // 'r' TSM2R, 'l' TSM2L, 'w' TSM2L with 8 rows per lane
+    const char *name;
+    int KC, BM, BNS, BOXM;
+    cudaError_t (*launch)(const BatchLaunch &, cudaStream_t);
+};
+const BatchClass *batch_class(char op, int kc);
+
 // Work partition of the persistent grid (shared by host sizing and kernels).
 struct Partition {
     int64_t num_rb;  // row blocks

@@ -15,6 +15,7 @@
 #include <mutex>
 #include <string>
 #include <utility>
+#include <vector>
 
 namespace tsm2 {
 namespace {
@@ -527,6 +528,111 @@ tsm2_status gemm_bf16(int64_t m, int64_t n, int64_t k, const void *A_hi, const v
     return TSM2_SUCCESS;
 }
 
+// ---- batched problems ----------------------------------------------------------
+
+}  // namespace
+}  // namespace tsm2
+
+struct tsm2_batch_plan_s {
+    struct Cls {
+        const tsm2::BatchClass *cls = nullptr;
+        std::vector<tsm2::ProbDesc> host;
+        int64_t ngroups = 0, nrb = 0;
+        double bytes = 0;
+        tsm2::ProbDesc *d_probs = nullptr;
+        void *d_ws = nullptr;     // counters, then partial-sum slots
+        size_t counter_bytes = 0;
+        int grid = 1;
+        cudaStream_t aux = nullptr;
+        cudaEvent_t done = nullptr;
+    };
+    struct Zero {
+        void *C;
+        int64_t ldc, m, k;
+    };
+    int dev = 0;
+    int sm_count = 0;
+    std::vector<Cls> classes;
+    std::vector<Zero> zeros;
+    cudaEvent_t fork = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t capture = nullptr;  // private stream the graph is captured on
+    bool serial = false;             // classes one after another, each on all SMs
+    double total_bytes = 0;
+};
+
+namespace tsm2 {
+namespace {
+
+void destroy_plan(tsm2_batch_plan_s *P) {
+    if (!P) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(P->dev);
+    if (P->graph) cudaGraphExecDestroy(P->graph);
+    for (auto &c : P->classes) {
+        if (c.d_probs) cudaFree(c.d_probs);
+        if (c.d_ws) cudaFree(c.d_ws);
+        if (c.aux) cudaStreamDestroy(c.aux);
+        if (c.done) cudaEventDestroy(c.done);
+    }
+    if (P->fork) cudaEventDestroy(P->fork);
+    if (P->capture) cudaStreamDestroy(P->capture);
+    cudaSetDevice(cur);
+    delete P;
+}
+
+tsm2_status plan_execute(tsm2_batch_plan_s *P, cudaStream_t stream, int only) {
+    cudaError_t e;
+    if (only < 0)
+        for (const auto &z : P->zeros) {
+            e = cudaMemset2DAsync(z.C, (size_t)z.ldc * 4, 0, (size_t)z.m * 4, (size_t)z.k, stream);
+            if (e != cudaSuccess) return cuda_error(e, "cudaMemset2DAsync");
+        }
+    DeviceState *dev = nullptr;
+    tsm2_status st = device_state(&dev);
+    if (st != TSM2_SUCCESS) return st;
+    const int nc = (int)P->classes.size();
+    if (only < 0 && P->serial) {
+        for (int i = 0; i < nc; ++i) {
+            tsm2_status s = plan_execute(P, stream, i);
+            if (s != TSM2_SUCCESS) return s;
+        }
+        return TSM2_SUCCESS;
+    }
+    if (only < 0 && nc > 1) {
+        e = cudaEventRecord(P->fork, stream);
+        if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+    }
+    for (int i = 0; i < nc; ++i) {
+        if (only >= 0 && i != only) continue;
+        auto &c = P->classes[i];
+        cudaStream_t s = (only >= 0 || i == 0) ? stream : c.aux;
+        if (only < 0 && i > 0) {
+            e = cudaStreamWaitEvent(s, P->fork, 0);
+            if (e != cudaSuccess) return cuda_error(e, "cudaStreamWaitEvent");
+        }
+        BatchLaunch L;
+        L.probs = c.d_probs;
+        L.nprob = (int)c.host.size();
+        L.ngroups = c.ngroups;
+        L.counters = static_cast<int *>(c.d_ws);
+        L.ws = static_cast<char *>(c.d_ws) + c.counter_bytes;
+        L.status = dev->status;
+        L.wait_ns = g_wait_ns;
+        L.grid = only >= 0 ? (int)std::min<int64_t>(P->sm_count, c.ngroups) : c.grid;
+        e = c.cls->launch(L, s);
+        if (e != cudaSuccess) return cuda_error(e, "batched kernel launch");
+        if (only < 0 && i > 0) {
+            e = cudaEventRecord(c.done, s);
+            if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+            e = cudaStreamWaitEvent(stream, c.done, 0);
+            if (e != cudaSuccess) return cuda_error(e, "cudaStreamWaitEvent");
+        }
+    }
+    return TSM2_SUCCESS;
+}
+
 // ---- allocation-free variant of the binary32 TSM2R bulk-copy path -----------
 //
 // Some callers cannot call cudaMalloc at all: a process whose device memory is
@@ -763,6 +869,215 @@ tsm2_status tsm2_split_bf16(int64_t rows, int64_t cols, const float *X, int64_t 
     cudaError_t e = split_bf16_launch(rows, cols, X, ldx, hi, lo, ldh, dev->sm_count, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? TSM2_SUCCESS : cuda_error(e, "split kernel launch");
 }
+
+tsm2_status tsm2_batch_plan_create_s(int nprob, const tsm2_problem_s *probs, int flags, tsm2_batch_plan_t *out) {
+    if (!out) return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_create_s: out is NULL");
+    *out = nullptr;
+    if (nprob < 0 || (nprob > 0 && !probs))
+        return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_create_s: bad problem list");
+    DeviceState *dev = nullptr;
+    tsm2_status st = device_state(&dev);
+    if (st != TSM2_SUCCESS) return st;
+    tsm2_batch_plan_s *P = new tsm2_batch_plan_s();
+    cudaGetDevice(&P->dev);
+    P->sm_count = dev->sm_count;
+    const bool wide = (flags & TSM2_BATCH_WIDE_L) != 0;
+    const bool merge_r = (flags & TSM2_BATCH_MERGE_R) != 0;
+    const bool merge_l = (flags & TSM2_BATCH_MERGE_L) != 0;
+    std::map<const BatchClass *, int> index;
+    for (int i = 0; i < nprob; ++i) {
+        const tsm2_problem_s &q = probs[i];
+        const char op = q.op == 'l' ? 'l' : (q.op == 'r' ? 'r' : 0);
+        if (!op) {
+            destroy_plan(P);
+            return set_error(TSM2_ERR_INVALID_VALUE, "batch problem %d: op must be 'r' or 'l'", i);
+        }
+        st = check_args("tsm2_batch_plan_create_s", q.m, q.n, q.k, q.A, q.lda, q.B, q.ldb, q.C, q.ldc, 4);
+        if (st != TSM2_SUCCESS) {
+            destroy_plan(P);
+            return st;
+        }
+        if (q.m == 0 || q.k == 0) continue;
+        if (q.n == 0) {
+            P->zeros.push_back({q.C, q.ldc, q.m, q.k});
+            continue;
+        }
+        if (op == 'l' && (q.n > 64 || q.k > 64)) {
+            destroy_plan(P);
+            return set_error(TSM2_ERR_UNSUPPORTED, "batch problem %d: TSM2L needs n, k <= 64", i);
+        }
+        if (!aligned16(q.A) || (q.lda * 4) % 16 != 0 || q.m >= (1ll << 31) - 4096 || q.n >= (1ll << 31) ||
+            (op == 'r' && (!aligned16(q.B) || (q.ldb * 4) % 16 != 0))) {
+            destroy_plan(P);
+            return set_error(TSM2_ERR_UNSUPPORTED,
+                             "batch problem %d: batched operands need 16-byte aligned bases and leading dimensions", i);
+        }
+        const int kcmax = op == 'l' ? 32 : 16;
+        for (int64_t c0 = 0; c0 < q.k; c0 += kcmax) {
+            const int kk = (int)std::min<int64_t>(kcmax, q.k - c0);
+            int kc = 2;
+            while (kc < kk) kc *= 2;
+            if (op == 'r' && merge_r) kc = 16;
+            if (op == 'l' && merge_l) kc = 32;
+            const BatchClass *cls = batch_class(op == 'l' && wide ? 'w' : op, kc);
+            if (!cls) {
+                destroy_plan(P);
+                return set_error(TSM2_ERR_UNSUPPORTED, "batch problem %d: no class for k chunk %d", i, kk);
+            }
+            auto it = index.find(cls);
+            if (it == index.end()) {
+                index[cls] = (int)P->classes.size();
+                P->classes.emplace_back();
+                P->classes.back().cls = cls;
+                it = index.find(cls);
+            }
+            auto &C = P->classes[it->second];
+            ProbDesc d;
+            std::memset(&d, 0, sizeof d);
+            const float *Bc = q.B + c0 * q.ldb;
+            st = encode_2d(&d.mapA, 4, q.A, q.m, q.n, q.lda, cls->BOXM, cls->BNS);
+            if (st == TSM2_SUCCESS && op == 'r') st = encode_2d(&d.mapB, 4, Bc, q.n, kk, q.ldb, cls->BNS, cls->KC);
+            if (st != TSM2_SUCCESS) {
+                destroy_plan(P);
+                return st;
+            }
+            const int64_t num_rb = (q.m + cls->BM - 1) / cls->BM;
+            const int64_t upr = (q.n + cls->BNS - 1) / cls->BNS;
+            d.m = q.m;
+            d.n = q.n;
+            d.ldb = q.ldb;
+            d.ldc = q.ldc;
+            d.B = Bc;
+            d.C = q.C + c0 * q.ldc;
+            d.k = kk;
+            d.upr = (int32_t)upr;
+            d.gran = op == 'l' ? (int32_t)upr : 1;
+            d.c_vec = aligned16(d.C) && (q.ldc * 4) % 16 == 0;
+            d.group_begin = C.ngroups;
+            d.rb_begin = C.nrb;
+            C.ngroups += op == 'l' ? num_rb : num_rb * upr;
+            C.nrb += num_rb;
+            C.bytes += 4.0 * ((double)q.m * q.n + (double)q.n * kk + (double)q.m * kk);
+            C.host.push_back(d);
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    for (auto &C : P->classes) {
+        P->total_bytes += C.bytes;
+        C.counter_bytes = ((size_t)C.nrb * sizeof(int) + 255) / 256 * 256;
+        const size_t slots = C.cls->op == 'r' ? (size_t)(P->sm_count + C.nrb) * C.cls->KC * C.cls->BM * 4 : 0;
+        if ((e = cudaMalloc(&C.d_probs, C.host.size() * sizeof(ProbDesc))) != cudaSuccess) break;
+        if ((e = cudaMemcpy(C.d_probs, C.host.data(), C.host.size() * sizeof(ProbDesc), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            break;
+        if ((e = cudaMalloc(&C.d_ws, C.counter_bytes + slots + 256)) != cudaSuccess) break;
+        if ((e = cudaMemset(C.d_ws, 0, C.counter_bytes)) != cudaSuccess) break;
+        if ((e = cudaStreamCreateWithFlags(&C.aux, cudaStreamNonBlocking)) != cudaSuccess) break;
+        if ((e = cudaEventCreateWithFlags(&C.done, cudaEventDisableTiming)) != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        destroy_plan(P);
+        return cuda_error(e, "tsm2_batch_plan_create_s");
+    }
+    // Default SM shares: proportional to each class's algorithmic bytes.
+    std::vector<double> w;
+    for (auto &C : P->classes) w.push_back(C.bytes);
+    std::vector<int> grids(w.size(), 1);
+    const int nc = (int)w.size();
+    if (nc > 0) {
+        int left = std::max(P->sm_count - nc, 0);
+        double tot = 0;
+        for (double x : w) tot += x;
+        for (int i = 0; i < nc; ++i) grids[i] += (int)((double)left * w[i] / (tot > 0 ? tot : 1));
+        for (int i = 0; i < nc; ++i) P->classes[i].grid = (int)std::min<int64_t>(grids[i], P->classes[i].ngroups);
+    }
+    *out = P;
+    return TSM2_SUCCESS;
+}
+
+tsm2_status tsm2_batch_plan_execute(tsm2_batch_plan_t plan, void *stream) {
+    if (!plan) return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_execute: NULL plan");
+    return plan_execute(plan, static_cast<cudaStream_t>(stream), -1);
+}
+
+tsm2_status tsm2_batch_plan_execute_class(tsm2_batch_plan_t plan, int cls, void *stream) {
+    if (!plan || cls < 0 || cls >= (int)plan->classes.size())
+        return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_execute_class: bad plan or class");
+    return plan_execute(plan, static_cast<cudaStream_t>(stream), cls);
+}
+
+tsm2_status tsm2_batch_plan_graph_launch(tsm2_batch_plan_t plan, void *stream_v) {
+    if (!plan) return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_graph_launch: NULL plan");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    cudaError_t e;
+    if (!plan->graph) {
+        // Captured once on the plan's own stream (the legacy default stream
+        // cannot be captured); the executable graph then runs on any stream.
+        e = cudaStreamBeginCapture(plan->capture, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_error(e, "cudaStreamBeginCapture");
+        tsm2_status st = plan_execute(plan, plan->capture, -1);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(plan->capture, &graph);
+        if (st != TSM2_SUCCESS) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&plan->graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            plan->graph = nullptr;
+            return cuda_error(e, "cudaGraphInstantiate");
+        }
+    }
+    e = cudaGraphLaunch(plan->graph, stream);
+    return e == cudaSuccess ? TSM2_SUCCESS : cuda_error(e, "cudaGraphLaunch");
+}
+
+int tsm2_batch_plan_num_classes(tsm2_batch_plan_t plan) { return plan ? (int)plan->classes.size() : 0; }
+
+tsm2_status tsm2_batch_plan_class_info(tsm2_batch_plan_t plan, int cls, const char **name, double *bytes, int *grid,
+                                       int *nprob) {
+    if (!plan || cls < 0 || cls >= (int)plan->classes.size())
+        return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_class_info: bad plan or class");
+    const auto &c = plan->classes[cls];
+    if (name) *name = c.cls->name;
+    if (bytes) *bytes = c.bytes;
+    if (grid) *grid = c.grid;
+    if (nprob) *nprob = (int)c.host.size();
+    return TSM2_SUCCESS;
+}
+
+tsm2_status tsm2_batch_plan_set_grids(tsm2_batch_plan_t plan, int ncls, const int *grids) {
+    if (!plan || ncls != (int)plan->classes.size() || (ncls > 0 && !grids))
+        return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_set_grids: bad arguments");
+    for (int i = 0; i < ncls; ++i) {
+        if (grids[i] < 1 || grids[i] > plan->sm_count)
+            return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_set_grids: grid %d out of [1, %d]", grids[i],
+                             plan->sm_count);
+    }
+    for (int i = 0; i < ncls; ++i)
+        plan->classes[i].grid = (int)std::min<int64_t>(grids[i], plan->classes[i].ngroups);
+    if (plan->graph) {
+        cudaGraphExecDestroy(plan->graph);
+        plan->graph = nullptr;
+    }
+    return TSM2_SUCCESS;
+}
+
+tsm2_status tsm2_batch_plan_set_serial(tsm2_batch_plan_t plan, int serial) {
+    if (!plan) return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_set_serial: NULL plan");
+    if (plan->serial != (serial != 0) && plan->graph) {
+        cudaGraphExecDestroy(plan->graph);
+        plan->graph = nullptr;
+    }
+    plan->serial = serial != 0;
+    return TSM2_SUCCESS;
+}
+
+void tsm2_batch_plan_destroy(tsm2_batch_plan_t plan) { destroy_plan(plan); }
 
 void tsm2_set_wait_budget_ns(int64_t ns) { g_wait_ns = ns < 0 ? 0 : ns; }
 

@@ -1,0 +1,106 @@
+// Compile-time tile configurations of the bulk-copy (TMA) kernels, shared by
+// the single-problem kernel (tsm2_stream.cu) and the batched kernel
+// (tsm2_batched.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace tsm2 {
+
+#ifndef TSM2_PACKED_FMA
+#define TSM2_PACKED_FMA 1
+#endif
+constexpr bool kPackedFma = TSM2_PACKED_FMA != 0;
+#ifndef TSM2_CQ
+#define TSM2_CQ 4
+#endif
+
+constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+constexpr int cmin(int a, int b) { return a < b ? a : b; }
+
+template <typename T_, int KC_, int NV_, int WR_, int WC_, int WK_, int JW_, int STAGES_, bool BRES_, int NRES_>
+struct Cfg {
+    using T = T_;
+    using VT = Vec16<T>;
+    using vec_t = typename VT::type;
+    static constexpr int V = VT::n;          // elements per 16-byte vector
+    static constexpr int KC = KC_;           // C columns per pass
+    static constexpr int NV = NV_;           // 16-byte row vectors per lane
+    static constexpr int WR = WR_;           // warps along rows
+    static constexpr int WC = WC_;           // warps along the inner dimension
+    static constexpr int WK = WK_;           // warps along the columns of C
+    static constexpr int KCW = KC_ / WK_;    // C columns per warp
+    static constexpr int JW = JW_;           // inner columns per warp per stage
+    static constexpr int STAGES = STAGES_;
+    static constexpr bool BRES = BRES_;      // B resident in shared memory
+    static constexpr int NRES = NRES_;       // inner extent reserved for resident B
+    static constexpr int R = NV * V;         // rows per lane
+    static constexpr int BM = WR * 32 * R;   // rows per row block
+    static constexpr int BNS = WC * JW;      // inner columns per stage
+    static constexpr int NW = WR * WC * WK;  // consumer warps
+    static constexpr int NT = NW * 32;       // consumer threads
+    static constexpr int THREADS = NT + 128; // plus one producer warpgroup (one lane works)
+    static_assert(NW == 8, "register split below assumes 2 consumer warpgroups");
+    static constexpr int BOXM = BM < 256 ? BM : 256;
+    static constexpr int NBOX = BM / BOXM;
+    static constexpr int JV = V;             // inner columns per B vector
+    static constexpr int CC = cmin(KC, 4);   // C columns per cross-warp reduction round
+    static constexpr int CQ = cmin(KCW, TSM2_CQ);  // C columns per group of the inner loop
+    static constexpr int A_STAGE = BM * BNS;                 // elements
+    static constexpr int B_STAGE = BRES ? 0 : BNS * KC;      // elements
+    static constexpr int RED = WC > 1 ? WC * CC * BM : 0;    // elements
+    static constexpr int BRES_ELEMS = BRES ? KC * NRES : 0;  // elements
+    static constexpr uint32_t TX_BYTES = (uint32_t)((A_STAGE + B_STAGE) * sizeof(T));
+    static constexpr size_t OFF_A = 0;
+    static constexpr size_t OFF_B = OFF_A + (size_t)STAGES * A_STAGE * sizeof(T);
+    static constexpr size_t OFF_BRES = OFF_B + (size_t)STAGES * B_STAGE * sizeof(T);
+    static constexpr size_t OFF_RED = OFF_BRES + (size_t)BRES_ELEMS * sizeof(T);
+    static constexpr size_t OFF_BAR = align_up(OFF_RED + (size_t)RED * sizeof(T), 16);
+    static constexpr size_t OFF_FLAGS = OFF_BAR + 2 * STAGES * sizeof(uint64_t);
+    static constexpr size_t SMEM = OFF_FLAGS + 32 + 128;  // + slack for 128-byte alignment
+
+    static_assert(JW % JV == 0, "a warp's columns must be whole B vectors");
+    static_assert((BNS * sizeof(T)) % 16 == 0, "TMA inner box extent must be 16-byte multiple");
+    static_assert((A_STAGE * sizeof(T)) % 128 == 0, "stage buffers stay 128-byte aligned");
+    static_assert((B_STAGE * sizeof(T)) % 128 == 0 || BRES, "stage buffers stay 128-byte aligned");
+    static_assert(BM % BOXM == 0 && (32 * V) <= BOXM, "a warp's vector row group fits one box");
+    static_assert(WC == 1 || (CC * BM) % NT == 0, "reduction rounds split evenly over threads");
+    static_assert(!BRES || NRES % BNS == 0, "resident B covers whole stages");
+    static_assert(KC % WK == 0 && (WK == 1 || (WC == 1 && BRES)), "C columns split only in the TSM2L schedule");
+    static_assert(SMEM <= 227 * 1024, "shared memory per block");
+};
+
+// Block index that owns group x under the partition gs(g) = floor(g*NG/G).
+__device__ __forceinline__ int64_t owner_of(int64_t x, int64_t G, int64_t NG) {
+    return ((x + 1) * G + NG - 1) / NG - 1;
+}
+
+// Register split (setmaxnreg): launched with 384 threads x 168 registers =
+// 64512; the producer warpgroup drops to 40 and the two consumer warpgroups
+// rise to 232: 4*32*40 + 8*32*232 = 64512, exactly the launch pool, and every
+// SM sub-partition (one producer warp + two consumer warps) holds
+// 32*(40 + 2*232) = 16128 <= 16384 registers.
+constexpr int kProducerRegs = 40;
+constexpr int kConsumerRegs = 232;
+static_assert(4 * 32 * kProducerRegs + 8 * 32 * kConsumerRegs <= 384 * 168, "register split exceeds launch pool");
+
+// TSM2R schedule: 1 x 8 warps split the inner columns of each stage.
+//   binary32: R = 8 rows per lane (two float4), BM = 256, BNS = 32.
+//   binary64: R = 4 rows per lane (two double2), BM = 128, BNS = 32.
+template <int KC> using R32 = Cfg<float, KC, 2, 1, 8, 1, 4, 5, false, 0>;
+template <int KC> using R64 = Cfg<double, KC, 2, 1, 8, 1, 4, 5, false, 0>;
+// TSM2L schedule: 8 x 1 warps split the rows; B (n <= 64) resident.
+//   binary32: R = 4, BM = 1024, BNS = 8.   binary64: R = 2, BM = 512, BNS = 8.
+//   KC = 32 splits the C columns over 2 x 4 warps (16 accumulated columns per
+//   lane, BM halves) to keep the accumulators in registers.
+template <int KC> using L32 = Cfg<float, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, 5, true, 64>;
+template <int KC> using L64 = Cfg<double, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, 5, true, 64>;
+// TSM2L schedule for tall A (binary32): R = 8 rows per lane, so every B value
+// read from shared memory (one wavefront per broadcast value) feeds twice the
+// FMAs; the C columns are split over WK = 1, 2, 4 warps (KC <= 8, 16, 32) so a
+// lane never holds more than 64 accumulators.  Chosen when there are enough
+// row blocks for an even spread over the SMs.
+template <int KC> using W32 = Cfg<float, KC, 2, (KC >= 32 ? 2 : KC >= 16 ? 4 : 8), 1, (KC >= 32 ? 4 : KC >= 16 ? 2 : 1),
+                                  (KC >= 16 ? 8 : 4), 5, true, 64>;
+
+}  // namespace tsm2

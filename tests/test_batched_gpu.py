@@ -1,0 +1,109 @@
+"""Batched plans (tsm2_batch_plan_*): every problem of an uneven batch against
+the CPU oracle, for every tile choice, grid share and launch mode."""
+import numpy as np
+import pytest
+
+import tsm2_inputs as ti
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_util import assert_parity  # noqa: E402
+
+
+def make_batch(seed=3):
+    import paper_2002_03258_gb300.batched as bt
+    shapes = ti.batch_shapes(seed, n_r=18, n_l=18, r_n=(1, 1500), r_k=(1, 20), l_m=(1, 60000), l_n=(1, 40))
+    shapes += [("r", 300, 0, 4), ("l", 0, 8, 8), ("r", 2000, 2000, 16), ("l", 70001, 64, 64)]
+    items = []
+    for idx, (op, m, n, k) in enumerate(shapes):
+        lda = (max(m, 1) + 3) // 4 * 4
+        ldb = (max(n, 1) + 3) // 4 * 4
+        ldc = lda + 4
+        A = ti.uniform_pm1(seed + idx, ti.MID_A, m, n, np.float32)
+        B = ti.uniform_pm1(seed + idx, ti.MID_B, n, k, np.float32)
+        tA = torch.zeros((max(n, 1), lda), device="cuda")
+        tB = torch.zeros((max(k, 1), ldb), device="cuda")
+        tC = torch.full((max(k, 1), ldc), float("nan"), device="cuda")
+        if m and n:
+            tA.t()[:m, :n].copy_(torch.from_numpy(np.ascontiguousarray(A)))
+        if n and k:
+            tB.t()[:n, :k].copy_(torch.from_numpy(np.ascontiguousarray(B)))
+        items.append(dict(op=op, m=m, n=n, k=k, A=A, B=B, tA=tA, tB=tB, tC=tC,
+                          p=bt.problem(op, m, n, k, tA.data_ptr(), lda, tB.data_ptr(), ldb, tC.data_ptr(), ldc)))
+    return items
+
+
+def check_all(items):
+    torch.cuda.synchronize()
+    for it in items:
+        m, k = it["m"], it["k"]
+        if m == 0 or k == 0:
+            continue
+        got = it["tC"].t()[:m, :k].cpu().numpy()
+        assert_parity(got, it["A"], it["B"], np.float32)
+
+
+@pytest.mark.parametrize("flags", [0, 1, 2, 4, 7])
+def test_batch_plan_parity(flags):
+    import paper_2002_03258_gb300 as pkg
+    import paper_2002_03258_gb300.batched as bt
+    items = make_batch()
+    plan = bt.BatchPlan([it["p"] for it in items], flags)
+    plan.execute(0)
+    assert pkg.tsm2_get_device_status(0) == 0
+    check_all(items)
+    first = [it["tC"].clone() for it in items]
+    # same plan as a CUDA graph, and with other SM shares: same results
+    for it in items:
+        it["tC"].fill_(float("nan"))
+    plan.graph_launch(0)
+    torch.cuda.synchronize()
+    for a, it in zip(first, items):
+        assert torch.equal(torch.nan_to_num(a, 7.0), torch.nan_to_num(it["tC"], 7.0))
+    ncls = len(plan.classes())
+    for grids in ([1] * ncls, [3] * ncls, [37] * ncls):
+        plan.set_grids(grids)
+        plan.graph_launch(0)
+        assert pkg.tsm2_get_device_status(0) == 0
+        check_all(items)
+    # classes one after another on all SMs (other split points: parity, not bits)
+    plan.set_serial(True)
+    for it in items:
+        it["tC"].fill_(float("nan"))
+    plan.graph_launch(0)
+    assert pkg.tsm2_get_device_status(0) == 0
+    check_all(items)
+    plan.close()
+
+
+def test_batch_rejects_unaligned_and_bad_args():
+    import paper_2002_03258_gb300 as pkg
+    import paper_2002_03258_gb300.batched as bt
+    t = torch.zeros(3 << 16, device="cuda")
+    base = t.data_ptr()
+    b_off, c_off = 1 << 18, 2 << 18  # bytes: A, B and C never overlap
+    with pytest.raises(pkg.TSM2Error) as e:  # lda * 4 not a multiple of 16 bytes
+        bt.BatchPlan([bt.problem("r", 33, 33, 4, base, 33, base + b_off, 36, base + c_off, 36)])
+    assert e.value.status == pkg.ERR_UNSUPPORTED
+    with pytest.raises(pkg.TSM2Error) as e:  # TSM2L with n > 64
+        bt.BatchPlan([bt.problem("l", 100, 65, 4, base, 100, base + b_off, 68, base + c_off, 100)])
+    assert e.value.status == pkg.ERR_UNSUPPORTED
+    with pytest.raises(pkg.TSM2Error) as e:
+        bt.BatchPlan([bt.problem("r", 10, 10, 2, base, 8, base + b_off, 12, base + c_off, 12)])  # lda < m
+    assert e.value.status == pkg.ERR_INVALID_VALUE
+
+
+def test_autotuner_picks_a_valid_plan(tmp_path):
+    from paper_2002_03258_gb300.autotune import autotune
+    items = make_batch(seed=5)
+    plan, rec = autotune([it["p"] for it in items], reps=2, cache_path=str(tmp_path / "tune.json"))
+    assert rec["ms"] > 0 and len(rec["trials"]) == 12
+    for it in items:
+        it["tC"].fill_(float("nan"))
+    plan.graph_launch(0)
+    check_all(items)
+    plan2, rec2 = autotune([it["p"] for it in items], cache_path=str(tmp_path / "tune.json"))
+    assert rec2.get("cached") and rec2["flags"] == rec["flags"]
+    plan.close()
+    plan2.close()

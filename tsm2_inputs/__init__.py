@@ -167,3 +167,28 @@ def padded(a: np.ndarray, ld: int, fill=np.nan) -> np.ndarray:
     buf = np.full((ld, cols), fill, dtype=a.dtype, order="F")
     buf[:rows, :] = a
     return buf
+
+
+def batch_shapes(seed: int = 0, n_r: int = 256, n_l: int = 256,
+                 r_n=(512, 8192), r_k=(2, 16), l_m=(2 ** 14, 2 ** 20), l_n=(4, 32)):
+    """Shapes of the uneven batch workload (draws of stream ``MID_BATCH``).
+
+    TSM2R problem i (i < n_r): square A, n = m from draw 2i, k from draw 2i+1.
+    TSM2L problem i: m from draw 2*n_r + 2i, n = k from draw 2*n_r + 2i + 1.
+    All bounds inclusive.  The list (R problems, then L problems) is then put
+    in the order of the argsort of draws 2*(n_r+n_l) + position.
+    Returns a list of (op, m, n, k).
+    """
+    out = []
+    for i in range(n_r):
+        n = int(uniform_int(seed, MID_BATCH, [2 * i], *r_n)[0])
+        k = int(uniform_int(seed, MID_BATCH, [2 * i + 1], *r_k)[0])
+        out.append(("r", n, n, k))
+    base = 2 * n_r
+    for i in range(n_l):
+        m = int(uniform_int(seed, MID_BATCH, [base + 2 * i], *l_m)[0])
+        n = int(uniform_int(seed, MID_BATCH, [base + 2 * i + 1], *l_n)[0])
+        out.append(("l", m, n, n))
+    keys = draws(stream_key(seed, MID_BATCH), np.arange(len(out)) + 2 * (n_r + n_l))
+    order = np.argsort(keys, kind="stable")
+    return [out[i] for i in order]
