@@ -153,14 +153,16 @@ tsm2_status tsm2_split_bf16(int64_t rows, int64_t cols, const float *X, int64_t 
  * device memory is wholly owned by another allocator (a framework's caching
  * pool that has reserved the free memory), or a latency-bound loop that
  * cannot pay for cudaMalloc and its implicit synchronisation.
- *  - Scratch: partial sums of row blocks split between thread blocks, and
- *    their arrival counters, live in a fixed 16 MiB array in device memory
- *    that every GPU loading the library holds until the process exits.  No
- *    call of this function allocates or frees device memory.
- *  - Limit: the partial sums must fit the array: m up to about 222,000 rows
- *    when a column chunk is 9..16 wide, more for narrower k (the exact bound
- *    is in the error message).  Larger problems return
- *    TSM2_ERR_UNSUPPORTED before anything is launched.
+ *  - Scratch: partial sums of row blocks split between thread blocks, their
+ *    arrival counters and (column chunks 9..16 wide) a packed n x 16 copy of
+ *    B live in a fixed 16 MiB array in device memory that every GPU loading
+ *    the library holds until the process exits.  No call of this function
+ *    allocates or frees device memory.
+ *  - Limit: those must fit the array: m up to about 222,000 rows when a
+ *    column chunk is 9..16 wide and n is small, fewer as n grows (64 bytes of
+ *    packed B per inner index), more for narrower k (the sizes are in the
+ *    error message).  Larger problems return TSM2_ERR_UNSUPPORTED before
+ *    anything is launched.
  *  - Set-up: the first call on each device looks up the array's device
  *    address (cudaGetSymbolAddress) with that device current; make that first
  *    call before any stream capture.

@@ -33,6 +33,17 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// Dynamic shared memory rounded up to `align` bytes.  The pad comes from the
+// shared-window address and is added to the array pointer itself, so the
+// result stays a shared-space pointer: loads through it compile to shared
+// loads, not generic ones (an integer round trip would lose that).
+template <unsigned kAlign>
+__device__ __forceinline__ unsigned char *smem_aligned(unsigned char *raw) {
+    static_assert((kAlign & (kAlign - 1)) == 0, "power of two");
+    const uint32_t a = smem_u32(raw);
+    return raw + ((kAlign - (a & (kAlign - 1))) & (kAlign - 1));
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -45,6 +45,7 @@ struct StreamShape {
     int BOXM;        // rows per TMA box
     int gran_rows;   // 1: split inner dim at stage granularity; 0: whole row blocks
     bool b_resident; // B loaded once into shared memory (requires n <= n_max_resident)
+    bool b_rowmajor; // streamed B read from its packed transpose (bt_pack_launch)
     int n_max_resident;
     int smem_bytes;
     int threads;
@@ -54,6 +55,13 @@ struct StreamShape {
 // Returns nullptr if no compiled configuration covers (elem, op, kc).
 const StreamShape *stream_shape(int elem, char op, int kc);
 cudaError_t stream_launch(const StreamShape *shape, const StreamLaunch &L, cudaStream_t stream);
+
+// Packs the first k (<= kc) columns of B (n x k, column-major, ldb) into Bt,
+// n rows of kc elements (Bt[j*kc + c] = B[j + c*ldb], zero for c >= k), the
+// layout read by configurations with b_rowmajor.  Bt must hold n*kc elements
+// and be 16-byte aligned.
+cudaError_t bt_pack_launch(int elem, int64_t n, int k, const void *B, int64_t ldb, int kc, void *Bt,
+                           cudaStream_t stream);
 
 // Element-wise fallback (any alignment), Algorithm 3 style.
 cudaError_t simple_launch(int elem, const GemmArgs &g, unsigned *status, cudaStream_t stream);
@@ -117,7 +125,7 @@ cudaError_t split_bf16_launch(int64_t rows, int64_t cols, const float *X, int64_
 // ---- batched problems (tsm2_batched.cu) --------------------------------------
 
 // Device-side descriptor of one problem of a batch class.
-struct alignas(64) ProbDesc {
+struct ProbDesc {  // aligned as its tensor maps
     CUtensorMap mapA;      // A: dims {m, n}, box {BOXM, BNS}
     CUtensorMap mapB;      // B: dims {n, k}, box {BNS, KC} (TSM2R classes)
     int64_t m, n, ldb, ldc;

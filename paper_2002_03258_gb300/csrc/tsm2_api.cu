@@ -267,7 +267,7 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
         L.g = g;
         st = encode_2d(&L.mapA, elem, A, m, n, lda, shape->BOXM, shape->BNS);
         if (st != TSM2_SUCCESS) return st;
-        if (!shape->b_resident) {
+        if (!shape->b_resident && !shape->b_rowmajor) {
             st = encode_2d(&L.mapB, elem, g.B, n, g.k, ldb, shape->BNS, shape->KC);
             if (st != TSM2_SUCCESS) return st;
         }
@@ -289,8 +289,17 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
         int *counters = nullptr;
         if (!shape->b_resident) {
             const size_t slots = (size_t)(grid + num_rb) * shape->KC * shape->BM * elem;
-            st = workspace(stream, (size_t)num_rb * sizeof(int), slots, &ws, &counters);
+            const size_t bt_off = (slots + 255) / 256 * 256;
+            const size_t bt_bytes = shape->b_rowmajor ? (size_t)n * shape->KC * elem : 0;
+            st = workspace(stream, (size_t)num_rb * sizeof(int), bt_off + bt_bytes, &ws, &counters);
             if (st != TSM2_SUCCESS) return st;
+            if (shape->b_rowmajor) {
+                void *bt = static_cast<char *>(ws) + bt_off;
+                e = bt_pack_launch(elem, n, g.k, g.B, ldb, shape->KC, bt, stream);
+                if (e != cudaSuccess) return cuda_error(e, "B packing kernel launch");
+                st = encode_2d(&L.mapB, elem, bt, shape->KC, n, shape->KC, shape->KC, shape->BNS);
+                if (st != TSM2_SUCCESS) return st;
+            }
         }
         L.ws = ws;
         L.counters = counters;
@@ -730,22 +739,30 @@ tsm2_status gemm_r32_noalloc(int64_t m, int64_t n, int64_t k, const float *A, in
         if (grid > ngroups) grid = ngroups;
         if (grid < 1) grid = 1;
         const size_t counter_bytes = (size_t)num_rb * sizeof(int);
+        // Partial-sum slots, then (row-major configurations) the packed B.
         const size_t slot_bytes = (size_t)(grid + num_rb) * shape->KC * shape->BM * elem;
-        if (counter_bytes > kNoAllocCounterBytes || slot_bytes > kNoAllocScratchBytes - kNoAllocCounterBytes)
+        const size_t bt_off = (slot_bytes + 255) / 256 * 256;
+        const size_t bt_bytes = shape->b_rowmajor ? (size_t)n * shape->KC * elem : 0;
+        const size_t data_cap = kNoAllocScratchBytes - kNoAllocCounterBytes;
+        if (counter_bytes > kNoAllocCounterBytes || bt_off + bt_bytes > data_cap)
             return set_error(TSM2_ERR_UNSUPPORTED,
-                             "%s: m=%lld needs %zu bytes of counters and %zu bytes of partial sums; the static "
-                             "scratch holds %zu and %zu (at most about %lld rows); use tsm2r_s instead",
-                             fn, (long long)m, counter_bytes, slot_bytes, kNoAllocCounterBytes,
-                             kNoAllocScratchBytes - kNoAllocCounterBytes,
-                             (long long)(((kNoAllocScratchBytes - kNoAllocCounterBytes) /
-                                          ((size_t)shape->KC * shape->BM * elem) - (size_t)grid) *
-                                         shape->BM));
+                             "%s: m=%lld n=%lld needs %zu bytes of counters and %zu bytes of partial sums and "
+                             "packed B; the static scratch holds %zu and %zu; use tsm2r_s instead",
+                             fn, (long long)m, (long long)n, counter_bytes, bt_off + bt_bytes, kNoAllocCounterBytes,
+                             data_cap);
         StreamLaunch L;
         std::memset(&L, 0, sizeof L);
         L.g = g;
         st = encode_2d(&L.mapA, elem, A, m, n, lda, shape->BOXM, shape->BNS);
         if (st != TSM2_SUCCESS) return st;
-        st = encode_2d(&L.mapB, elem, g.B, n, g.k, ldb, shape->BNS, shape->KC);
+        if (shape->b_rowmajor) {
+            void *bt = static_cast<char *>(scratch) + kNoAllocCounterBytes + bt_off;
+            e = bt_pack_launch(elem, n, g.k, g.B, ldb, shape->KC, bt, stream);
+            if (e != cudaSuccess) return cuda_error(e, "B packing kernel launch");
+            st = encode_2d(&L.mapB, elem, bt, shape->KC, n, shape->KC, shape->KC, shape->BNS);
+        } else {
+            st = encode_2d(&L.mapB, elem, g.B, n, g.k, ldb, shape->BNS, shape->KC);
+        }
         if (st != TSM2_SUCCESS) return st;
         // The array keeps whatever the previous call left; the arrival
         // counters must start at zero.

@@ -81,7 +81,7 @@ tsm2t_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     using T = typename K::T;
     using vec_t = typename K::vec_t;
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    unsigned char *smem = smem_aligned<128>(smem_raw);
     T *sA = reinterpret_cast<T *>(smem);
     T *sD = reinterpret_cast<T *>(smem + K::OFF_D);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + K::OFF_BAR);

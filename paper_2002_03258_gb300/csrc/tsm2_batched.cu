@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
     static_assert(sizeof(T) == 4, "the batched kernel is binary32");
     static_assert(K::WC > 1 || K::BRES, "row-split schedules run whole row blocks only (no partial-sum path)");
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(align_up(reinterpret_cast<uintptr_t>(smem_raw), 128));
+    unsigned char *smem = smem_aligned<128>(smem_raw);
     T *sA = reinterpret_cast<T *>(smem + K::OFF_A);
     T *sB = reinterpret_cast<T *>(smem + K::OFF_B);
     T *sBres = reinterpret_cast<T *>(smem + K::OFF_BRES);

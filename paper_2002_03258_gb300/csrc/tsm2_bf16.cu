@@ -140,7 +140,7 @@ __device__ __forceinline__ int64_t owner_b(int64_t x, int64_t G, int64_t NG) { r
 __global__ void __launch_bounds__(192, 1)
 bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ CUtensorMap mapLo, const BParams p) {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *smem = smem_aligned<1024>(smem_raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kSmemBudget);
     uint64_t *full = bars;                   // [stages] TMA landed
     uint64_t *empty = bars + kMaxStages;     // [stages] MMAs done with the stage

@@ -18,7 +18,8 @@ constexpr bool kPackedFma = TSM2_PACKED_FMA != 0;
 constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
 
-template <typename T_, int KC_, int NV_, int WR_, int WC_, int WK_, int JW_, int STAGES_, bool BRES_, int NRES_>
+template <typename T_, int KC_, int NV_, int WR_, int WC_, int WK_, int JW_, int STAGES_, bool BRES_, int NRES_,
+          bool BT_ = false, int BOXM_ = 0>
 struct Cfg {
     using T = T_;
     using VT = Vec16<T>;
@@ -34,6 +35,11 @@ struct Cfg {
     static constexpr int STAGES = STAGES_;
     static constexpr bool BRES = BRES_;      // B resident in shared memory
     static constexpr int NRES = NRES_;       // inner extent reserved for resident B
+    // B in shared memory row-major (element (j, c) at j*KC + c) instead of
+    // column-major: one 16-byte load gives two column pairs of one inner index,
+    // so packed FMAs pair C columns and duplicate the A value (R per inner
+    // index) instead of the B value (KCW per inner index).
+    static constexpr bool BT = BT_;
     static constexpr int R = NV * V;         // rows per lane
     static constexpr int BM = WR * 32 * R;   // rows per row block
     static constexpr int BNS = WC * JW;      // inner columns per stage
@@ -41,7 +47,7 @@ struct Cfg {
     static constexpr int NT = NW * 32;       // consumer threads
     static constexpr int THREADS = NT + 128; // plus one producer warpgroup (one lane works)
     static_assert(NW == 8, "register split below assumes 2 consumer warpgroups");
-    static constexpr int BOXM = BM < 256 ? BM : 256;
+    static constexpr int BOXM = BOXM_ > 0 ? BOXM_ : (BM < 256 ? BM : 256);
     static constexpr int NBOX = BM / BOXM;
     static constexpr int JV = V;             // inner columns per B vector
     static constexpr int CC = cmin(KC, 4);   // C columns per cross-warp reduction round
@@ -59,7 +65,7 @@ struct Cfg {
     static constexpr size_t OFF_FLAGS = OFF_BAR + 2 * STAGES * sizeof(uint64_t);
     static constexpr size_t SMEM = OFF_FLAGS + 32 + 128;  // + slack for 128-byte alignment
 
-    static_assert(JW % JV == 0, "a warp's columns must be whole B vectors");
+    static_assert(BT || JW % JV == 0, "a warp's columns must be whole B vectors");
     static_assert((BNS * sizeof(T)) % 16 == 0, "TMA inner box extent must be 16-byte multiple");
     static_assert((A_STAGE * sizeof(T)) % 128 == 0, "stage buffers stay 128-byte aligned");
     static_assert((B_STAGE * sizeof(T)) % 128 == 0 || BRES, "stage buffers stay 128-byte aligned");
@@ -68,6 +74,7 @@ struct Cfg {
     static_assert(!BRES || NRES % BNS == 0, "resident B covers whole stages");
     static_assert(KC % WK == 0 && (WK == 1 || (WC == 1 && BRES)), "C columns split only in the TSM2L schedule");
     static_assert(SMEM <= 227 * 1024, "shared memory per block");
+    static_assert(!BT || (sizeof(T) == 4 && KCW % 4 == 0), "row-major B: binary32, whole 16-byte column groups");
 };
 
 // Block index that owns group x under the partition gs(g) = floor(g*NG/G).
@@ -87,7 +94,19 @@ static_assert(4 * 32 * kProducerRegs + 8 * 32 * kConsumerRegs <= 384 * 168, "reg
 // TSM2R schedule: 1 x 8 warps split the inner columns of each stage.
 //   binary32: R = 8 rows per lane (two float4), BM = 256, BNS = 32.
 //   binary64: R = 4 rows per lane (two double2), BM = 128, BNS = 32.
-template <int KC> using R32 = Cfg<float, KC, 2, 1, 8, 1, 4, 5, false, 0>;
+//   KC = 16 keeps B row-major in shared memory (half the operand duplication).
+#ifndef TSM2_R16_NV
+#define TSM2_R16_NV 2
+#endif
+#ifndef TSM2_R16_JW
+#define TSM2_R16_JW 4
+#endif
+#ifndef TSM2_R16_STAGES
+#define TSM2_R16_STAGES 5
+#endif
+template <int KC>
+using R32 = Cfg<float, KC, (KC >= 16 ? TSM2_R16_NV : 2), 1, 8, 1, (KC >= 16 ? TSM2_R16_JW : 4),
+                (KC >= 16 ? TSM2_R16_STAGES : 5), false, 0, (KC >= 16), (KC >= 16 && TSM2_R16_NV == 3 ? 128 : 0)>;
 template <int KC> using R64 = Cfg<double, KC, 2, 1, 8, 1, 4, 5, false, 0>;
 // TSM2L schedule: 8 x 1 warps split the rows; B (n <= 64) resident.
 //   binary32: R = 4, BM = 1024, BNS = 8.   binary64: R = 2, BM = 512, BNS = 8.

@@ -71,7 +71,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     using T = typename K::T;
     using vec_t = typename K::vec_t;
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(align_up(reinterpret_cast<uintptr_t>(smem_raw), 128));
+    unsigned char *smem = smem_aligned<128>(smem_raw);
     T *sA = reinterpret_cast<T *>(smem + K::OFF_A);
     T *sB = reinterpret_cast<T *>(smem + K::OFF_B);
     T *sBres = reinterpret_cast<T *>(smem + K::OFF_BRES);
@@ -108,12 +108,13 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
         fence_mbar_init();
     }
     if constexpr (K::BRES) {
-        // Whole of B (n <= NRES) once per block, column c at sBres[c*NRES + j],
-        // zero beyond n and k so padded lanes contribute exact zeros.
+        // Whole of B (n <= NRES) once per block, column c at sBres[c*NRES + j]
+        // (row-major configurations: sBres[j*KC + c]), zero beyond n and k so
+        // padded lanes contribute exact zeros.
         const T *B = static_cast<const T *>(p.B);
         for (int t = threadIdx.x; t < K::KC * K::NRES; t += K::THREADS) {
-            const int j = t % K::NRES;
-            const int c = t / K::NRES;
+            const int j = K::BT ? t / K::KC : t % K::NRES;
+            const int c = K::BT ? t % K::KC : t / K::NRES;
             sBres[t] = (j < p.n && c < p.k) ? B[j + (int64_t)c * p.ldb] : T(0);
         }
     }
@@ -147,7 +148,10 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 #pragma unroll
                 for (int q = 0; q < K::NBOX; ++q)
                     tma_load_2d_hint(dstA + q * K::BOXM * K::BNS, &mapA, x0 + q * K::BOXM, y0, &full[s], policy);
-                if constexpr (!K::BRES) tma_load_2d(sB + (size_t)s * K::B_STAGE, &mapB, y0, 0, &full[s]);
+                // Row-major configurations read B from its packed transpose
+                // (KC x n, inner coordinate 0: aligned).
+                if constexpr (!K::BRES)
+                    tma_load_2d(sB + (size_t)s * K::B_STAGE, &mapB, K::BT ? 0 : y0, K::BT ? y0 : 0, &full[s]);
                 issued |= 1u << s;
                 last_par = (last_par & ~(1u << s)) | (ph << s);
                 if (++s == K::STAGES) { s = 0; ph ^= 1u; }
@@ -207,6 +211,47 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             const T *a_st = sA + (size_t)s * K::A_STAGE;
             const T *b_st;
             int bstride;
+            if constexpr (K::BT) {
+                // Row-major B: row j of the stage at b_st + j*KC.  Per inner
+                // index: the lane's R values of A, then for each group of four
+                // C columns one 16-byte broadcast load giving two column
+                // pairs, each pair updated by packed FMAs with (a, a).
+                b_st = K::BRES ? sBres + (size_t)jc * K::BNS * K::KC : sB + (size_t)s * K::B_STAGE;
+#pragma unroll
+                for (int jj = 0; jj < K::JW; ++jj) {
+                    const int j = wc * K::JW + jj;
+                    float a[K::R];
+#pragma unroll
+                    for (int v = 0; v < K::NV; ++v) {
+                        const int r = row_of(v);
+                        const int q = r / K::BOXM;
+                        const int rr = r - q * K::BOXM;
+                        const float4 x =
+                            *reinterpret_cast<const float4 *>(a_st + q * K::BOXM * K::BNS + j * K::BOXM + rr);
+                        a[v * 4 + 0] = x.x;
+                        a[v * 4 + 1] = x.y;
+                        a[v * 4 + 2] = x.z;
+                        a[v * 4 + 3] = x.w;
+                    }
+                    const T *brow = b_st + j * K::KC + kbase;
+#pragma unroll
+                    for (int c0 = 0; c0 < K::KCW; c0 += 4) {
+                        const float4 bq = *reinterpret_cast<const float4 *>(brow + c0);
+                        const float2 b01 = make_float2(bq.x, bq.y);
+                        const float2 b23 = make_float2(bq.z, bq.w);
+#pragma unroll
+                        for (int r = 0; r < K::R; ++r) {
+                            const float2 aa = make_float2(a[r], a[r]);
+                            const float2 t0 = __ffma2_rn(aa, b01, make_float2(acc[r][c0], acc[r][c0 + 1]));
+                            const float2 t1 = __ffma2_rn(aa, b23, make_float2(acc[r][c0 + 2], acc[r][c0 + 3]));
+                            acc[r][c0] = t0.x;
+                            acc[r][c0 + 1] = t0.y;
+                            acc[r][c0 + 2] = t1.x;
+                            acc[r][c0 + 3] = t1.y;
+                        }
+                    }
+                }
+            } else {
             if constexpr (K::BRES) {
                 b_st = sBres + jc * K::BNS;
                 bstride = K::NRES;
@@ -262,6 +307,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                         }
                 }
             }
+            }  // row-major B
         }
         // Release the stage to the producer.  A warp that gave up releases
         // nothing more: the producer then stops too, so no copy is ever issued
@@ -496,6 +542,7 @@ StreamShape shape_of(const char *name) {
     s.BOXM = K::BOXM;
     s.gran_rows = K::BRES ? 0 : 1;
     s.b_resident = K::BRES;
+    s.b_rowmajor = K::BT && !K::BRES;
     s.n_max_resident = K::NRES;
     s.smem_bytes = (int)K::SMEM;
     s.threads = K::THREADS;
@@ -526,6 +573,31 @@ const Entry kEntries[] = {
 };
 
 }  // namespace
+
+template <typename T>
+__global__ void bt_pack_kernel(int64_t n, int k, const T *__restrict__ B, int64_t ldb, int kc, T *__restrict__ Bt) {
+    const int64_t total = n * kc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / kc;
+        const int c = (int)(t - j * kc);
+        Bt[t] = c < k ? B[j + (int64_t)c * ldb] : T(0);
+    }
+}
+
+cudaError_t bt_pack_launch(int elem, int64_t n, int k, const void *B, int64_t ldb, int kc, void *Bt,
+                           cudaStream_t stream) {
+    const int64_t total = n * kc;
+    const int threads = 256;
+    const int64_t want = (total + threads - 1) / threads;
+    const int blocks = (int)(want < 1024 ? (want > 0 ? want : 1) : 1024);
+    if (elem == 8)
+        bt_pack_kernel<double><<<blocks, threads, 0, stream>>>(n, k, static_cast<const double *>(B), ldb, kc,
+                                                              static_cast<double *>(Bt));
+    else
+        bt_pack_kernel<float><<<blocks, threads, 0, stream>>>(n, k, static_cast<const float *>(B), ldb, kc,
+                                                             static_cast<float *>(Bt));
+    return cudaGetLastError();
+}
 
 const StreamShape *stream_shape(int elem, char op, int kc) {
     for (const Entry &en : kEntries)
