@@ -127,9 +127,10 @@ cudaError_t split_bf16_launch(int64_t rows, int64_t cols, const float *X, int64_
 // Device-side descriptor of one problem of a batch class.
 struct ProbDesc {  // aligned as its tensor maps
     CUtensorMap mapA;      // A: dims {m, n}, box {BOXM, BNS}
-    CUtensorMap mapB;      // B: dims {n, k}, box {BNS, KC} (TSM2R classes)
+    CUtensorMap mapB;      // TSM2R classes: B dims {n, k}, box {BNS, KC}; row-major classes: Bt dims {KC, n}, box {KC, BNS}
     int64_t m, n, ldb, ldc;
-    const void *B;         // TSM2L classes: B is read with ordinary loads
+    const void *B;         // TSM2L classes read B with ordinary loads; row-major TSM2R classes pack it
+    void *Bt;              // row-major TSM2R classes: packed n x KC copy of B (plan workspace)
     void *C;
     int64_t group_begin;   // first work group of the problem in the class numbering
     int64_t rb_begin;      // first row block (counters and partial-sum slots)
@@ -149,6 +150,7 @@ struct BatchClass {
     char op;  // 'r' TSM2R, 'l' TSM2L, 'w' TSM2L with 8 rows per lane
     const char *name;
     int KC, BM, BNS, BOXM;
+    bool b_rowmajor;  // TSM2R class reading B from packed row-major copies (ProbDesc::Bt)
     cudaError_t (*launch)(const BatchLaunch &, cudaStream_t);
 };
 const BatchClass *batch_class(char op, int kc);

@@ -953,7 +953,10 @@ tsm2_status tsm2_batch_plan_create_s(int nprob, const tsm2_problem_s *probs, int
             std::memset(&d, 0, sizeof d);
             const float *Bc = q.B + c0 * q.ldb;
             st = encode_2d(&d.mapA, 4, q.A, q.m, q.n, q.lda, cls->BOXM, cls->BNS);
-            if (st == TSM2_SUCCESS && op == 'r') st = encode_2d(&d.mapB, 4, Bc, q.n, kk, q.ldb, cls->BNS, cls->KC);
+            // Row-major classes encode B's map over the packed copy once the
+            // plan workspace exists (below).
+            if (st == TSM2_SUCCESS && op == 'r' && !cls->b_rowmajor)
+                st = encode_2d(&d.mapB, 4, Bc, q.n, kk, q.ldb, cls->BNS, cls->KC);
             if (st != TSM2_SUCCESS) {
                 destroy_plan(P);
                 return st;
@@ -983,11 +986,28 @@ tsm2_status tsm2_batch_plan_create_s(int nprob, const tsm2_problem_s *probs, int
         P->total_bytes += C.bytes;
         C.counter_bytes = ((size_t)C.nrb * sizeof(int) + 255) / 256 * 256;
         const size_t slots = C.cls->op == 'r' ? (size_t)(P->sm_count + C.nrb) * C.cls->KC * C.cls->BM * 4 : 0;
+        // Row-major TSM2R classes: packed B copies after the partial-sum slots.
+        const size_t bt_base = C.counter_bytes + (slots + 255) / 256 * 256;
+        size_t bt_bytes = 0;
+        if (C.cls->b_rowmajor)
+            for (const auto &d : C.host) bt_bytes += ((size_t)d.n * C.cls->KC * 4 + 255) / 256 * 256;
+        if ((e = cudaMalloc(&C.d_ws, bt_base + bt_bytes + 256)) != cudaSuccess) break;
+        if (C.cls->b_rowmajor) {
+            size_t off = bt_base;
+            for (auto &d : C.host) {
+                d.Bt = static_cast<char *>(C.d_ws) + off;
+                off += ((size_t)d.n * C.cls->KC * 4 + 255) / 256 * 256;
+                tsm2_status s2 = encode_2d(&d.mapB, 4, d.Bt, C.cls->KC, d.n, C.cls->KC, C.cls->KC, C.cls->BNS);
+                if (s2 != TSM2_SUCCESS) {
+                    destroy_plan(P);
+                    return s2;
+                }
+            }
+        }
         if ((e = cudaMalloc(&C.d_probs, C.host.size() * sizeof(ProbDesc))) != cudaSuccess) break;
         if ((e = cudaMemcpy(C.d_probs, C.host.data(), C.host.size() * sizeof(ProbDesc), cudaMemcpyHostToDevice)) !=
             cudaSuccess)
             break;
-        if ((e = cudaMalloc(&C.d_ws, C.counter_bytes + slots + 256)) != cudaSuccess) break;
         if ((e = cudaMemset(C.d_ws, 0, C.counter_bytes)) != cudaSuccess) break;
         if ((e = cudaStreamCreateWithFlags(&C.aux, cudaStreamNonBlocking)) != cudaSuccess) break;
         if ((e = cudaEventCreateWithFlags(&C.done, cudaEventDisableTiming)) != cudaSuccess) break;

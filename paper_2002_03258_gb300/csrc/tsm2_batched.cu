@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
 #pragma unroll
                     for (int q = 0; q < K::NBOX; ++q)
                         tma_load_2d_hint(dstA + q * K::BOXM * K::BNS, &pd->mapA, x0 + q * K::BOXM, y0, &full[s], policy);
-                    if constexpr (!K::BRES) tma_load_2d(sB + (size_t)s * K::B_STAGE, &pd->mapB, y0, 0, &full[s]);
+                    if constexpr (!K::BRES)  // row-major classes: the packed copy, inner coordinate 0
+                        tma_load_2d(sB + (size_t)s * K::B_STAGE, &pd->mapB, K::BT ? 0 : y0, K::BT ? y0 : 0, &full[s]);
                     issued |= 1u << s;
                     last_par = (last_par & ~(1u << s)) | (ph << s);
                     if (++s == K::STAGES) { s = 0; ph ^= 1u; }
@@ -159,7 +160,8 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
                 named_bar_sync(1, K::NT);
                 const T *Bp = static_cast<const T *>(pd->B);
                 for (int t = tid; t < K::KC * K::NRES; t += K::NT) {
-                    const int j = t % K::NRES, c = t / K::NRES;
+                    const int j = K::BT ? t / K::KC : t % K::NRES;
+                    const int c = K::BT ? t % K::KC : t / K::NRES;
                     sBres[t] = (j < pd->n && c < pd->k) ? Bp[j + (int64_t)c * pd->ldb] : T(0);
                 }
                 named_bar_sync(1, K::NT);
@@ -187,50 +189,13 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
                 const T *b_st;
                 int bstride;
                 if constexpr (K::BRES) {
-                    b_st = sBres + jc * K::BNS;
+                    b_st = K::BT ? sBres + (size_t)jc * K::BNS * K::KC : sBres + jc * K::BNS;
                     bstride = K::NRES;
                 } else {
                     b_st = sB + (size_t)s * K::B_STAGE;
                     bstride = K::BNS;
                 }
-#pragma unroll
-                for (int jj = 0; jj < K::JW; jj += K::JV) {
-                    const int j = wc * K::JW + jj;
-                    T a[K::JV][K::R];
-#pragma unroll
-                    for (int jv = 0; jv < K::JV; ++jv)
-#pragma unroll
-                        for (int v = 0; v < K::NV; ++v) {
-                            const int r = row_of(v);
-                            const int q = r / K::BOXM, rr = r - q * K::BOXM;
-                            const vec_t x =
-                                *reinterpret_cast<const vec_t *>(a_st + q * K::BOXM * K::BNS + (j + jv) * K::BOXM + rr);
-#pragma unroll
-                            for (int e = 0; e < K::V; ++e) a[jv][v * K::V + e] = K::VT::get(x, e);
-                        }
-#pragma unroll
-                    for (int c0 = 0; c0 < K::KCW; c0 += K::CQ) {
-                        vec_t bv[K::CQ];
-#pragma unroll
-                        for (int cq = 0; cq < K::CQ; ++cq)
-                            bv[cq] = *reinterpret_cast<const vec_t *>(b_st + (kbase + c0 + cq) * bstride + j);
-#pragma unroll
-                        for (int jv = 0; jv < K::JV; ++jv)
-#pragma unroll
-                            for (int cq = 0; cq < K::CQ; ++cq) {
-                                const int c = c0 + cq;
-                                const float b = K::VT::get(bv[cq], jv);
-                                const float2 bb = make_float2(b, b);
-#pragma unroll
-                                for (int r = 0; r < K::R; r += 2) {
-                                    const float2 tt = __ffma2_rn(make_float2(a[jv][r], a[jv][r + 1]), bb,
-                                                                 make_float2(acc[r][c], acc[r + 1][c]));
-                                    acc[r][c] = tt.x;
-                                    acc[r + 1][c] = tt.y;
-                                }
-                            }
-                    }
-                }
+                consume_stage<K>(a_st, b_st, bstride, wc, kbase, row_of(0), acc);
             }
             if (!aborted) {
                 __syncwarp();
@@ -353,6 +318,24 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
     }
 }
 
+// Packed row-major copies of B for the problems of a row-major TSM2R class:
+// Bt[j*kc + c] = B[j + c*ldb] for c < k, zero for k <= c < kc.  Run before
+// every execution of the class, so the plan always sees the current B.
+__global__ void batch_bt_pack_kernel(const ProbDesc *__restrict__ probs, int nprob, int kc) {
+    for (int i = blockIdx.y; i < nprob; i += gridDim.y) {
+        const ProbDesc &d = probs[i];
+        const float *B = static_cast<const float *>(d.B);
+        float *Bt = static_cast<float *>(d.Bt);
+        const int64_t total = d.n * kc;
+        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+             t += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t j = t / kc;
+            const int c = (int)(t - j * kc);
+            Bt[t] = c < d.k ? B[j + (int64_t)c * d.ldb] : 0.0f;
+        }
+    }
+}
+
 template <class K>
 cudaError_t launch_batched(const BatchLaunch &L, cudaStream_t stream) {
     static std::mutex mu;
@@ -376,6 +359,12 @@ cudaError_t launch_batched(const BatchLaunch &L, cudaStream_t stream) {
     p.counters = L.counters;
     p.status = L.status;
     p.wait_ns = L.wait_ns;
+    if constexpr (K::BT && !K::BRES) {
+        const dim3 pg(8, (unsigned)(L.nprob < 65535 ? L.nprob : 65535));
+        batch_bt_pack_kernel<<<pg, 256, 0, stream>>>(L.probs, L.nprob, K::KC);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     batched_kernel<K><<<L.grid, 384, K::SMEM, stream>>>(p);
     return cudaGetLastError();
 }
@@ -389,6 +378,7 @@ BatchClass class_of(char op, const char *name) {
     c.BM = K::BM;
     c.BNS = K::BNS;
     c.BOXM = K::BOXM;
+    c.b_rowmajor = K::BT && !K::BRES;
     c.launch = &launch_batched<K>;
     return c;
 }

@@ -77,6 +77,112 @@ struct Cfg {
     static_assert(!BT || (sizeof(T) == 4 && KCW % 4 == 0), "row-major B: binary32, whole 16-byte column groups");
 };
 
+// One pipeline stage of one consumer warp (Alg. 2's inner update, with the
+// warp's share of the stage): for j over the warp's JW inner indices,
+// ascending, acc[r][c] += A(rbase + row(r), j) * B(j, kbase + c).
+//   a_st:  the stage's A tile, NBOX boxes of BOXM rows x BNS inner columns,
+//          rows contiguous;
+//   b_st:  the stage's B, row-major (K::BT: element (j, c) at b_st[j*KC + c])
+//          or column-major (column c at b_st + c*bstride);
+//   rbase: first row of the lane's first 16-byte row vector (vector v covers
+//          rows rbase + v*32*V .. + V-1).
+// Every accumulator sees the same sequence of single-rounding FMAs in both
+// layouts, so results do not depend on the layout.
+template <class K>
+__device__ __forceinline__ void consume_stage(const typename K::T *a_st, const typename K::T *b_st, int bstride,
+                                              int wc, int kbase, int rbase, typename K::T (&acc)[K::R][K::KCW]) {
+    using T = typename K::T;
+    using vec_t = typename K::vec_t;
+    if constexpr (K::BT) {
+        // Per inner index: the lane's R values of A, then for each group of
+        // four C columns one 16-byte broadcast load giving two column pairs,
+        // each updated by a packed FMA with (a, a).
+#pragma unroll
+        for (int jj = 0; jj < K::JW; ++jj) {
+            const int j = wc * K::JW + jj;
+            float a[K::R];
+#pragma unroll
+            for (int v = 0; v < K::NV; ++v) {
+                const int r = rbase + v * 32 * K::V;
+                const int q = r / K::BOXM;
+                const int rr = r - q * K::BOXM;
+                const float4 x = *reinterpret_cast<const float4 *>(a_st + q * K::BOXM * K::BNS + j * K::BOXM + rr);
+                a[v * 4 + 0] = x.x;
+                a[v * 4 + 1] = x.y;
+                a[v * 4 + 2] = x.z;
+                a[v * 4 + 3] = x.w;
+            }
+            const T *brow = b_st + j * K::KC + kbase;
+#pragma unroll
+            for (int c0 = 0; c0 < K::KCW; c0 += 4) {
+                const float4 bq = *reinterpret_cast<const float4 *>(brow + c0);
+                const float2 b01 = make_float2(bq.x, bq.y);
+                const float2 b23 = make_float2(bq.z, bq.w);
+#pragma unroll
+                for (int r = 0; r < K::R; ++r) {
+                    const float2 aa = make_float2(a[r], a[r]);
+                    const float2 t0 = __ffma2_rn(aa, b01, make_float2(acc[r][c0], acc[r][c0 + 1]));
+                    const float2 t1 = __ffma2_rn(aa, b23, make_float2(acc[r][c0 + 2], acc[r][c0 + 3]));
+                    acc[r][c0] = t0.x;
+                    acc[r][c0 + 1] = t0.y;
+                    acc[r][c0 + 2] = t1.x;
+                    acc[r][c0 + 3] = t1.y;
+                }
+            }
+        }
+    } else {
+        // Column-major B: one 16-byte load gives JV consecutive inner indices
+        // of one C column; A for those JV indices is loaded first.
+#pragma unroll
+        for (int jj = 0; jj < K::JW; jj += K::JV) {
+            const int j = wc * K::JW + jj;  // stage-local inner column of the first vector lane
+            T a[K::JV][K::R];
+#pragma unroll
+            for (int jv = 0; jv < K::JV; ++jv)
+#pragma unroll
+                for (int v = 0; v < K::NV; ++v) {
+                    const int r = rbase + v * 32 * K::V;
+                    const int q = r / K::BOXM;
+                    const int rr = r - q * K::BOXM;
+                    const vec_t x =
+                        *reinterpret_cast<const vec_t *>(a_st + q * K::BOXM * K::BNS + (j + jv) * K::BOXM + rr);
+#pragma unroll
+                    for (int e = 0; e < K::V; ++e) a[jv][v * K::V + e] = K::VT::get(x, e);
+                }
+            // C columns in groups of CQ: consecutive FMAs of a group hit
+            // different accumulators, so no FMA waits on the previous one.
+#pragma unroll
+            for (int c0 = 0; c0 < K::KCW; c0 += K::CQ) {
+                vec_t bv[K::CQ];
+#pragma unroll
+                for (int cq = 0; cq < K::CQ; ++cq)
+                    bv[cq] = *reinterpret_cast<const vec_t *>(b_st + (kbase + c0 + cq) * bstride + j);
+#pragma unroll
+                for (int jv = 0; jv < K::JV; ++jv)
+#pragma unroll
+                    for (int cq = 0; cq < K::CQ; ++cq) {
+                        const int c = c0 + cq;
+                        const T b = K::VT::get(bv[cq], jv);
+                        if constexpr (kPackedFma && sizeof(T) == 4) {
+                            // Two rows per packed FFMA2: half the FMA issue slots.
+                            const float2 bb = make_float2(b, b);
+#pragma unroll
+                            for (int r = 0; r < K::R; r += 2) {
+                                const float2 t = __ffma2_rn(make_float2(a[jv][r], a[jv][r + 1]), bb,
+                                                            make_float2(acc[r][c], acc[r + 1][c]));
+                                acc[r][c] = t.x;
+                                acc[r + 1][c] = t.y;
+                            }
+                        } else {
+#pragma unroll
+                            for (int r = 0; r < K::R; ++r) acc[r][c] = fma(a[jv][r], b, acc[r][c]);
+                        }
+                    }
+            }
+        }
+    }
+}
+
 // Block index that owns group x under the partition gs(g) = floor(g*NG/G).
 __device__ __forceinline__ int64_t owner_of(int64_t x, int64_t G, int64_t NG) {
     return ((x + 1) * G + NG - 1) / NG - 1;
@@ -108,18 +214,39 @@ template <int KC>
 using R32 = Cfg<float, KC, (KC >= 16 ? TSM2_R16_NV : 2), 1, 8, 1, (KC >= 16 ? TSM2_R16_JW : 4),
                 (KC >= 16 ? TSM2_R16_STAGES : 5), false, 0, (KC >= 16), (KC >= 16 && TSM2_R16_NV == 3 ? 128 : 0)>;
 template <int KC> using R64 = Cfg<double, KC, 2, 1, 8, 1, 4, 5, false, 0>;
+// TSM2L: resident B row-major wherever a warp's C columns are whole groups of
+// four (the B load at block start transposes; no packed copy needed).
+#ifndef TSM2_L_BT
+#define TSM2_L_BT 1
+#endif
 // TSM2L schedule: 8 x 1 warps split the rows; B (n <= 64) resident.
 //   binary32: R = 4, BM = 1024, BNS = 8.   binary64: R = 2, BM = 512, BNS = 8.
 //   KC = 32 splits the C columns over 2 x 4 warps (16 accumulated columns per
 //   lane, BM halves) to keep the accumulators in registers.
-template <int KC> using L32 = Cfg<float, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, 5, true, 64>;
+template <int KC>
+using L32 = Cfg<float, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, 5, true, 64,
+                (TSM2_L_BT != 0 && (KC / (KC >= 32 ? 2 : 1)) % 4 == 0)>;
 template <int KC> using L64 = Cfg<double, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, 5, true, 64>;
 // TSM2L schedule for tall A (binary32): R = 8 rows per lane, so every B value
 // read from shared memory (one wavefront per broadcast value) feeds twice the
 // FMAs; the C columns are split over WK = 1, 2, 4 warps (KC <= 8, 16, 32) so a
 // lane never holds more than 64 accumulators.  Chosen when there are enough
 // row blocks for an even spread over the SMs.
-template <int KC> using W32 = Cfg<float, KC, 2, (KC >= 32 ? 2 : KC >= 16 ? 4 : 8), 1, (KC >= 32 ? 4 : KC >= 16 ? 2 : 1),
-                                  (KC >= 16 ? 8 : 4), 5, true, 64>;
+#ifndef TSM2_W32_VAR
+#define TSM2_W32_VAR 0
+#endif
+struct WShape {
+    int nv, wr, wk, jw, st;
+};
+constexpr WShape w32_shape(int kc) {
+    return kc >= 32 ? (TSM2_W32_VAR == 1   ? WShape{2, 4, 2, 8, 5}
+                       : TSM2_W32_VAR == 2 ? WShape{4, 2, 4, 8, 5}
+                                           : WShape{2, 2, 4, 8, 5})
+         : kc >= 16 ? (TSM2_W32_VAR == 1 ? WShape{2, 8, 1, 8, 3} : WShape{2, 4, 2, 8, 5})
+                    : WShape{2, 8, 1, 4, 5};
+}
+template <int KC>
+using W32 = Cfg<float, KC, w32_shape(KC).nv, w32_shape(KC).wr, 1, w32_shape(KC).wk, w32_shape(KC).jw,
+                w32_shape(KC).st, true, 64, (TSM2_L_BT != 0 && (KC / w32_shape(KC).wk) % 4 == 0)>;
 
 }  // namespace tsm2

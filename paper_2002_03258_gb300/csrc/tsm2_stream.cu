@@ -211,103 +211,14 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             const T *a_st = sA + (size_t)s * K::A_STAGE;
             const T *b_st;
             int bstride;
-            if constexpr (K::BT) {
-                // Row-major B: row j of the stage at b_st + j*KC.  Per inner
-                // index: the lane's R values of A, then for each group of four
-                // C columns one 16-byte broadcast load giving two column
-                // pairs, each pair updated by packed FMAs with (a, a).
-                b_st = K::BRES ? sBres + (size_t)jc * K::BNS * K::KC : sB + (size_t)s * K::B_STAGE;
-#pragma unroll
-                for (int jj = 0; jj < K::JW; ++jj) {
-                    const int j = wc * K::JW + jj;
-                    float a[K::R];
-#pragma unroll
-                    for (int v = 0; v < K::NV; ++v) {
-                        const int r = row_of(v);
-                        const int q = r / K::BOXM;
-                        const int rr = r - q * K::BOXM;
-                        const float4 x =
-                            *reinterpret_cast<const float4 *>(a_st + q * K::BOXM * K::BNS + j * K::BOXM + rr);
-                        a[v * 4 + 0] = x.x;
-                        a[v * 4 + 1] = x.y;
-                        a[v * 4 + 2] = x.z;
-                        a[v * 4 + 3] = x.w;
-                    }
-                    const T *brow = b_st + j * K::KC + kbase;
-#pragma unroll
-                    for (int c0 = 0; c0 < K::KCW; c0 += 4) {
-                        const float4 bq = *reinterpret_cast<const float4 *>(brow + c0);
-                        const float2 b01 = make_float2(bq.x, bq.y);
-                        const float2 b23 = make_float2(bq.z, bq.w);
-#pragma unroll
-                        for (int r = 0; r < K::R; ++r) {
-                            const float2 aa = make_float2(a[r], a[r]);
-                            const float2 t0 = __ffma2_rn(aa, b01, make_float2(acc[r][c0], acc[r][c0 + 1]));
-                            const float2 t1 = __ffma2_rn(aa, b23, make_float2(acc[r][c0 + 2], acc[r][c0 + 3]));
-                            acc[r][c0] = t0.x;
-                            acc[r][c0 + 1] = t0.y;
-                            acc[r][c0 + 2] = t1.x;
-                            acc[r][c0 + 3] = t1.y;
-                        }
-                    }
-                }
-            } else {
             if constexpr (K::BRES) {
-                b_st = sBres + jc * K::BNS;
+                b_st = K::BT ? sBres + (size_t)jc * K::BNS * K::KC : sBres + jc * K::BNS;
                 bstride = K::NRES;
             } else {
                 b_st = sB + (size_t)s * K::B_STAGE;
                 bstride = K::BNS;
             }
-#pragma unroll
-            for (int jj = 0; jj < K::JW; jj += K::JV) {
-                const int j = wc * K::JW + jj;  // stage-local inner column of the first vector lane
-                T a[K::JV][K::R];
-#pragma unroll
-                for (int jv = 0; jv < K::JV; ++jv)
-#pragma unroll
-                    for (int v = 0; v < K::NV; ++v) {
-                        const int r = row_of(v);
-                        const int q = r / K::BOXM;
-                        const int rr = r - q * K::BOXM;
-                        const vec_t x =
-                            *reinterpret_cast<const vec_t *>(a_st + q * K::BOXM * K::BNS + (j + jv) * K::BOXM + rr);
-#pragma unroll
-                        for (int e = 0; e < K::V; ++e) a[jv][v * K::V + e] = K::VT::get(x, e);
-                    }
-                // C columns in groups of CQ: consecutive FMAs of a group hit
-                // different accumulators, so no FMA waits on the previous one.
-#pragma unroll
-#pragma unroll
-                for (int c0 = 0; c0 < K::KCW; c0 += K::CQ) {
-                    vec_t bv[K::CQ];
-#pragma unroll
-                    for (int cq = 0; cq < K::CQ; ++cq)
-                        bv[cq] = *reinterpret_cast<const vec_t *>(b_st + (kbase + c0 + cq) * bstride + j);
-#pragma unroll
-                    for (int jv = 0; jv < K::JV; ++jv)
-#pragma unroll
-                        for (int cq = 0; cq < K::CQ; ++cq) {
-                            const int c = c0 + cq;
-                            const T b = K::VT::get(bv[cq], jv);
-                            if constexpr (kPackedFma && sizeof(T) == 4) {
-                                // Two rows per packed FFMA2: half the FMA issue slots.
-                                const float2 bb = make_float2(b, b);
-#pragma unroll
-                                for (int r = 0; r < K::R; r += 2) {
-                                    const float2 t = __ffma2_rn(make_float2(a[jv][r], a[jv][r + 1]), bb,
-                                                                make_float2(acc[r][c], acc[r + 1][c]));
-                                    acc[r][c] = t.x;
-                                    acc[r + 1][c] = t.y;
-                                }
-                            } else {
-#pragma unroll
-                                for (int r = 0; r < K::R; ++r) acc[r][c] = fma(a[jv][r], b, acc[r][c]);
-                            }
-                        }
-                }
-            }
-            }  // row-major B
+            consume_stage<K>(a_st, b_st, bstride, wc, kbase, row_of(0), acc);
         }
         // Release the stage to the producer.  A warp that gave up releases
         // nothing more: the producer then stops too, so no copy is ever issued
