@@ -557,12 +557,18 @@ def run_gpu(args):
         torch.cuda.empty_cache()
 
     # ---- end to end through the C ABI with host buffers --------------------------------------
-    h_in, h_out = [], []
+    # tsm2r_s_host / tsm2l_s_host: A, B, C in page-locked host memory; each
+    # call streams A to the device in row chunks, overlapping copy-in, the
+    # product and the copy-out of C (all inside the timed region).
+    h_in, h_out, h_shared = [], [], {}
     for w in work32:
-        hA = torch.empty((w["n"], w["m"]), dtype=w["A"].dtype, pin_memory=True).t()
-        hA.copy_(w["A"])
-        hB = torch.empty((w["B"].shape[1], w["n"]), dtype=w["A"].dtype, pin_memory=True).t()
-        hB.copy_(w["B"])
+        key = w["A"].data_ptr()  # cases that share a device A share its host copy
+        if key not in h_shared:
+            h_shared[key] = torch.empty((w["n"], w["m"]), dtype=w["A"].dtype, pin_memory=True).t()
+            h_shared[key].copy_(w["A"])
+        hA = h_shared[key]
+        hB = torch.empty((w["k"], w["n"]), dtype=w["A"].dtype, pin_memory=True).t()
+        hB.copy_(w["B"][:, :w["k"]])
         hC = torch.empty((w["k"], w["m"]), dtype=w["A"].dtype, pin_memory=True).t()
         h_in.append((hA, hB))
         h_out.append(hC)
@@ -570,17 +576,22 @@ def run_gpu(args):
     e2e_steps = max(1, min(args.steps, 5))
     h2d = sum(w["A"].numel() * w["es"] + w["n"] * w["k"] * w["es"] for w in work32)
     d2h = sum(w["m"] * w["k"] * w["es"] for w in work32)
+    host_fn = {"r": pkg.tsm2r_s_host, "l": pkg.tsm2l_s_host}
+
+    def e2e_step():
+        for (hA, hB), hC, w in zip(h_in, h_out, work32):
+            pkg.check(host_fn[w["op"]](w["m"], w["n"], w["k"], hA.data_ptr(), w["m"], hB.data_ptr(), w["n"],
+                                       hC.data_ptr(), w["m"], sh))
+
+    e2e_step()  # staging buffers allocated outside the timed region
+    torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e_start.record(stream)
     for _ in range(e2e_steps):
-        for (hA, hB), hC, w in zip(h_in, h_out, work32):
-            w["A"].copy_(hA, non_blocking=True)
-            w["B"][:, :w["k"]].copy_(hB[:, :w["k"]], non_blocking=True)
-            pkg.check(call(w))
-            hC.copy_(w["C"][:, :w["k"]], non_blocking=True)
+        e2e_step()
     e_end.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e_start.elapsed_time(e_end) / e2e_steps

@@ -147,6 +147,32 @@ tsm2_status tsm2r_bf16(int64_t m, int64_t n, int64_t k, const uint16_t *A_hi, co
 tsm2_status tsm2_split_bf16(int64_t rows, int64_t cols, const float *X, int64_t ldx,
                             uint16_t *hi, uint16_t *lo, int64_t ldh, void *stream);
 
+/* Host-resident operands: the same products with A, B and C in host memory
+ * (page-locked memory gives full copy/compute overlap; pageable memory works
+ * at lower speed).  The paper keeps its operands in device memory; these are
+ * a library convenience with no counterpart there.
+ *  - Work: B is copied once; A streams to the device in chunks of whole rows
+ *    (about 256 MiB, at least 64 KiB per column piece, multiples of 256 rows)
+ *    through two device staging slots; each chunk's C rows are copied back
+ *    as soon as its product is done.  Copy-in of the next chunk overlaps the
+ *    product and copy-out of the current one.
+ *  - Ordering: the work starts after everything already queued on `stream`,
+ *    and `stream` waits for the last C rows to reach the host: synchronise
+ *    `stream` before reading C.  The host buffers must stay valid until then.
+ *  - Memory: the staging slots are device memory the library allocates on
+ *    first use and grows as needed (held until tsm2_shutdown).  Calls on one
+ *    device are serialised on one set of staging slots.
+ *  - Errors: the argument rules of the device entry points (pointers are
+ *    host pointers here); n == 0 waits for `stream` and zeroes C on the host. */
+tsm2_status tsm2r_s_host(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb,
+                         float *C, int64_t ldc, void *stream);
+tsm2_status tsm2r_d_host(int64_t m, int64_t n, int64_t k, const double *A, int64_t lda, const double *B,
+                         int64_t ldb, double *C, int64_t ldc, void *stream);
+tsm2_status tsm2l_s_host(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb,
+                         float *C, int64_t ldc, void *stream);
+tsm2_status tsm2l_d_host(int64_t m, int64_t n, int64_t k, const double *A, int64_t lda, const double *B,
+                         int64_t ldb, double *C, int64_t ldc, void *stream);
+
 /* TSM2R, binary32, allocating nothing.  The paper has no counterpart: this
  * is a library convenience.  Same arguments, result and error contract as
  * tsm2r_s, for callers that cannot call cudaMalloc at all -- a process whose

@@ -781,6 +781,195 @@ tsm2_status gemm_r32_noalloc(int64_t m, int64_t n, int64_t k, const float *A, in
     return TSM2_SUCCESS;
 }
 
+// ---- host-resident operands: row-chunk pipeline ---------------------------
+//
+// A is streamed to the device in chunks of whole rows (a 2-D copy: mc rows of
+// each of the n columns) into one of two staging slots.  Three streams run
+// the stages: the copy-in stream fills slot (c & 1) with chunk c, the compute
+// stream runs the device product on it, the copy-out stream returns its C
+// rows.  Copy-in of chunk c+1 overlaps the product and copy-out of chunk c,
+// and copy-in of chunk c+2 waits only for copy-out of chunk c (which itself
+// followed the product), so the link stays busy in both directions.
+
+struct HostPipe {
+    cudaStream_t in = nullptr, comp = nullptr, out = nullptr;
+    cudaEvent_t entry = nullptr, b_ready = nullptr, done = nullptr;
+    cudaEvent_t a_ready[2] = {}, c_ready[2] = {}, slot_free[2] = {};
+    void *dA[2] = {}, *dC[2] = {}, *dB = nullptr;
+    size_t a_bytes = 0, c_bytes = 0, b_bytes = 0;
+    std::mutex mu;
+};
+std::mutex g_pipe_mu;
+std::map<int, HostPipe *> g_pipes;
+
+#ifndef TSM2_HOST_CHUNK_MB
+#define TSM2_HOST_CHUNK_MB 256
+#endif
+#ifndef TSM2_HOST_MIN_SEGMENT_KB
+#define TSM2_HOST_MIN_SEGMENT_KB 64
+#endif
+constexpr size_t kHostChunkBytes = (size_t)TSM2_HOST_CHUNK_MB << 20;        // target bytes of A per chunk
+constexpr size_t kHostMinSegment = (size_t)TSM2_HOST_MIN_SEGMENT_KB << 10;  // least bytes per column piece
+
+void pipe_free_buffers(HostPipe *P) {
+    for (int i = 0; i < 2; ++i) {
+        if (P->dA[i]) cudaFree(P->dA[i]);
+        if (P->dC[i]) cudaFree(P->dC[i]);
+        P->dA[i] = P->dC[i] = nullptr;
+    }
+    if (P->dB) cudaFree(P->dB);
+    P->dB = nullptr;
+    P->a_bytes = P->c_bytes = P->b_bytes = 0;
+}
+
+void pipe_destroy(HostPipe *P) {
+    pipe_free_buffers(P);
+    for (cudaStream_t s : {P->in, P->comp, P->out})
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : {P->entry, P->b_ready, P->done, P->a_ready[0], P->a_ready[1], P->c_ready[0], P->c_ready[1],
+                          P->slot_free[0], P->slot_free[1]})
+        if (e) cudaEventDestroy(e);
+    delete P;
+}
+
+tsm2_status pipe_for_device(HostPipe **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    auto it = g_pipes.find(dev);
+    if (it != g_pipes.end()) {
+        *out = it->second;
+        return TSM2_SUCCESS;
+    }
+    HostPipe *P = new HostPipe();
+    for (cudaStream_t *s : {&P->in, &P->comp, &P->out})
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&P->entry, &P->b_ready, &P->done, &P->a_ready[0], &P->a_ready[1], &P->c_ready[0],
+                            &P->c_ready[1], &P->slot_free[0], &P->slot_free[1]})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        pipe_destroy(P);
+        return cuda_error(e, "host pipeline set-up");
+    }
+    g_pipes[dev] = P;
+    *out = P;
+    return TSM2_SUCCESS;
+}
+
+// Grows a device buffer; the pipeline's streams are idle when this runs (the
+// caller synchronises them first).
+tsm2_status grow(void **p, size_t *have, size_t want) {
+    if (*have >= want && *p) return TSM2_SUCCESS;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    cudaError_t e = cudaMalloc(p, want);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_error(e, "cudaMalloc(host pipeline staging)");
+    }
+    *have = want;
+    return TSM2_SUCCESS;
+}
+
+tsm2_status gemm_host(const char *fn, char op, int elem, int64_t m, int64_t n, int64_t k, const void *hA, int64_t lda,
+                      const void *hB, int64_t ldb, void *hC, int64_t ldc, void *stream_v) {
+    tsm2_status st = check_args(fn, m, n, k, hA, lda, hB, ldb, hC, ldc, elem);
+    if (st != TSM2_SUCCESS) return st;
+    if (op == 'l' && (n > 64 || k > 64))
+        return set_error(TSM2_ERR_UNSUPPORTED, "%s: TSM2L needs n <= 64 and k <= 64 (got n=%lld k=%lld)", fn,
+                         (long long)n, (long long)k);
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    cudaError_t e;
+    if (m == 0 || k == 0) {
+        t_last_config = "empty";
+        return TSM2_SUCCESS;
+    }
+    if (n == 0) {  // C = 0 on the host, after the caller's pending work
+        e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+        for (int64_t c = 0; c < k; ++c) std::memset(static_cast<char *>(hC) + (size_t)(c * ldc) * elem, 0, (size_t)m * elem);
+        t_last_config = "zero-fill";
+        return TSM2_SUCCESS;
+    }
+    HostPipe *P = nullptr;
+    st = pipe_for_device(&P);
+    if (st != TSM2_SUCCESS) return st;
+    std::lock_guard<std::mutex> lk(P->mu);
+
+    // Rows per chunk: about kHostChunkBytes of A but column pieces of at
+    // least kHostMinSegment bytes (a 2-D copy moves one piece per column),
+    // a multiple of 256 rows (whole row blocks of every schedule); the
+    // staging leading dimension is the chunk height rounded to 16 bytes.
+    const int64_t vec = 16 / elem;
+    int64_t mc = (int64_t)(kHostChunkBytes / ((size_t)n * elem));
+    if (mc < (int64_t)(kHostMinSegment / elem)) mc = (int64_t)(kHostMinSegment / elem);
+    mc = mc / 256 * 256;
+    if (mc < 256) mc = 256;
+    if (mc > m) mc = m;
+    const int64_t ldd = (mc + vec - 1) / vec * vec;
+    const int64_t ldbd = (n + vec - 1) / vec * vec;
+    const size_t a_need = (size_t)ldd * n * elem, c_need = (size_t)ldd * k * elem, b_need = (size_t)ldbd * k * elem;
+    if (P->a_bytes < a_need || P->c_bytes < c_need || P->b_bytes < b_need) {
+        for (cudaStream_t s : {P->in, P->comp, P->out}) {
+            e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize(host pipeline)");
+        }
+        size_t ah = P->a_bytes, ch = P->c_bytes;
+        for (int i = 0; i < 2; ++i) {
+            size_t a_have = ah, c_have = ch;
+            if ((st = grow(&P->dA[i], &a_have, a_need)) != TSM2_SUCCESS) return st;
+            if ((st = grow(&P->dC[i], &c_have, c_need)) != TSM2_SUCCESS) return st;
+            if (i == 1) {
+                P->a_bytes = a_have;
+                P->c_bytes = c_have;
+            }
+        }
+        if ((st = grow(&P->dB, &P->b_bytes, b_need)) != TSM2_SUCCESS) return st;
+    }
+
+    // Everything starts after the caller's pending work on `stream`.
+    if ((e = cudaEventRecord(P->entry, stream)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+    for (cudaStream_t s : {P->in, P->comp, P->out})
+        if ((e = cudaStreamWaitEvent(s, P->entry, 0)) != cudaSuccess) return cuda_error(e, "cudaStreamWaitEvent");
+    e = cudaMemcpy2DAsync(P->dB, (size_t)ldbd * elem, hB, (size_t)ldb * elem, (size_t)n * elem, (size_t)k,
+                          cudaMemcpyHostToDevice, P->in);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy2DAsync(B)");
+    if ((e = cudaEventRecord(P->b_ready, P->in)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+    if ((e = cudaStreamWaitEvent(P->comp, P->b_ready, 0)) != cudaSuccess) return cuda_error(e, "cudaStreamWaitEvent");
+
+    const char *config = "";
+    int64_t chunk = 0;
+    for (int64_t i0 = 0; i0 < m; i0 += mc, ++chunk) {
+        const int slot = (int)(chunk & 1);
+        const int64_t rows = (m - i0) < mc ? (m - i0) : mc;
+        if (chunk >= 2 && (e = cudaStreamWaitEvent(P->in, P->slot_free[slot], 0)) != cudaSuccess)
+            return cuda_error(e, "cudaStreamWaitEvent");
+        e = cudaMemcpy2DAsync(P->dA[slot], (size_t)ldd * elem, static_cast<const char *>(hA) + (size_t)i0 * elem,
+                              (size_t)lda * elem, (size_t)rows * elem, (size_t)n, cudaMemcpyHostToDevice, P->in);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy2DAsync(A chunk)");
+        if ((e = cudaEventRecord(P->a_ready[slot], P->in)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+        if ((e = cudaStreamWaitEvent(P->comp, P->a_ready[slot], 0)) != cudaSuccess)
+            return cuda_error(e, "cudaStreamWaitEvent");
+        st = gemm(fn, op, elem, rows, n, k, P->dA[slot], ldd, P->dB, ldbd, P->dC[slot], ldd, P->comp);
+        if (st != TSM2_SUCCESS) return st;
+        config = t_last_config;
+        if ((e = cudaEventRecord(P->c_ready[slot], P->comp)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+        if ((e = cudaStreamWaitEvent(P->out, P->c_ready[slot], 0)) != cudaSuccess)
+            return cuda_error(e, "cudaStreamWaitEvent");
+        e = cudaMemcpy2DAsync(static_cast<char *>(hC) + (size_t)i0 * elem, (size_t)ldc * elem, P->dC[slot],
+                              (size_t)ldd * elem, (size_t)rows * elem, (size_t)k, cudaMemcpyDeviceToHost, P->out);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy2DAsync(C chunk)");
+        if ((e = cudaEventRecord(P->slot_free[slot], P->out)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+    }
+    // The caller's stream resumes once the last C rows are on the host.
+    if ((e = cudaEventRecord(P->done, P->out)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+    if ((e = cudaStreamWaitEvent(stream, P->done, 0)) != cudaSuccess) return cuda_error(e, "cudaStreamWaitEvent");
+    t_last_config = config;
+    return TSM2_SUCCESS;
+}
+
 }  // namespace
 }  // namespace tsm2
 
@@ -836,9 +1025,18 @@ tsm2_status tsm2_get_device_status(void *stream) {
 }
 
 void tsm2_shutdown(void) {
-    std::lock_guard<std::mutex> lk(g_mu);
     int cur = 0;
     cudaGetDevice(&cur);
+    {
+        std::lock_guard<std::mutex> lk(g_pipe_mu);
+        for (auto &kv : g_pipes) {
+            cudaSetDevice(kv.first);
+            for (cudaStream_t s : {kv.second->in, kv.second->comp, kv.second->out}) cudaStreamSynchronize(s);
+            pipe_destroy(kv.second);
+        }
+        g_pipes.clear();
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
     for (auto &kv : g_ws) {
         if (!kv.second.ptr) continue;
         cudaSetDevice(kv.first.first);
@@ -846,6 +1044,26 @@ void tsm2_shutdown(void) {
     }
     g_ws.clear();
     cudaSetDevice(cur);
+}
+
+tsm2_status tsm2r_s_host(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb,
+                         float *C, int64_t ldc, void *stream) {
+    return gemm_host("tsm2r_s_host", 'r', 4, m, n, k, A, lda, B, ldb, C, ldc, stream);
+}
+
+tsm2_status tsm2r_d_host(int64_t m, int64_t n, int64_t k, const double *A, int64_t lda, const double *B, int64_t ldb,
+                         double *C, int64_t ldc, void *stream) {
+    return gemm_host("tsm2r_d_host", 'r', 8, m, n, k, A, lda, B, ldb, C, ldc, stream);
+}
+
+tsm2_status tsm2l_s_host(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb,
+                         float *C, int64_t ldc, void *stream) {
+    return gemm_host("tsm2l_s_host", 'l', 4, m, n, k, A, lda, B, ldb, C, ldc, stream);
+}
+
+tsm2_status tsm2l_d_host(int64_t m, int64_t n, int64_t k, const double *A, int64_t lda, const double *B, int64_t ldb,
+                         double *C, int64_t ldc, void *stream) {
+    return gemm_host("tsm2l_d_host", 'l', 8, m, n, k, A, lda, B, ldb, C, ldc, stream);
 }
 
 tsm2_status tsm2r_t_d(int64_t m, int64_t n, int64_t k, const double *A, int64_t lda, const double *dC, int64_t lddc,

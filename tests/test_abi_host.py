@@ -47,7 +47,8 @@ def test_every_declared_symbol_is_exported(lib):
 FAKE = 1 << 20  # never dereferenced: every call below fails or returns before any launch
 
 
-@pytest.mark.parametrize("fn", ["tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s"])
+@pytest.mark.parametrize("fn", ["tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s",
+                                "tsm2r_s_host", "tsm2r_d_host", "tsm2l_s_host", "tsm2l_d_host"])
 @pytest.mark.parametrize("args,why", [
     ((-1, 4, 2, FAKE, 4, FAKE * 2, 4, FAKE * 3, 4), "negative m"),
     ((4, -4, 2, FAKE, 4, FAKE * 2, 4, FAKE * 3, 4), "negative n"),
@@ -67,14 +68,15 @@ def test_invalid_arguments(lib, fn, args, why):
     assert pkg.tsm2_get_last_error_string() != "no error"
 
 
-@pytest.mark.parametrize("fn", ["tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s"])
+@pytest.mark.parametrize("fn", ["tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s",
+                                "tsm2r_s_host", "tsm2r_d_host", "tsm2l_s_host", "tsm2l_d_host"])
 def test_quick_returns_without_device(lib, fn):
     # m == 0 or k == 0: nothing to do, no CUDA call is made.
     assert getattr(pkg, fn)(0, 5, 3, 0, 1, FAKE, 5, 0, 1, 0) == pkg.SUCCESS
     assert getattr(pkg, fn)(5, 5, 0, FAKE, 5, FAKE * 2, 5, 0, 5, 0) == pkg.SUCCESS
 
 
-@pytest.mark.parametrize("fn", ["tsm2l_d", "tsm2l_s"])
+@pytest.mark.parametrize("fn", ["tsm2l_d", "tsm2l_s", "tsm2l_s_host", "tsm2l_d_host"])
 def test_tsm2l_limits(lib, fn):
     assert getattr(pkg, fn)(100, 65, 8, FAKE, 100, FAKE * 2, 65, FAKE * 3, 100, 0) == pkg.ERR_UNSUPPORTED
     assert getattr(pkg, fn)(100, 8, 65, FAKE, 100, FAKE * 2, 8, FAKE * 3, 100, 0) == pkg.ERR_UNSUPPORTED
