@@ -556,6 +556,46 @@ def run_gpu(args):
         del keep, probs, loop_calls
         torch.cuda.empty_cache()
 
+    # ---- TSM2R / TSM2L crossover and the TSM2X choice -------------------------------------------
+    crossover = None
+    if not args.no_crossover:
+        rows_x = []
+        worst = 1.0
+        for m in (15360, 1 << 20):
+            for n in (4, 16, 64, 256, 1024):
+                k = 16
+                A = torch.empty((n, m), dtype=torch.float32, device=dev).t()
+                B = torch.empty((k, n), dtype=torch.float32, device=dev).t()
+                C = torch.empty((k, m), dtype=torch.float32, device=dev).t()
+                pkg.check(lib.tsm2_fill_uniform_s(m, n, 0, ti.MID_A, A.data_ptr(), m, sh))
+                pkg.check(lib.tsm2_fill_uniform_s(n, k, 0, ti.MID_B, B.data_ptr(), n, sh))
+                nbytes = 4 * (m * n + n * k + m * k)
+                rec = {"m": m, "n": n, "k": k}
+                for name, fn in (("tsm2r", pkg.tsm2r_s), ("tsm2l", pkg.tsm2l_s), ("tsm2x", pkg.tsm2x_s)):
+                    def one(fn=fn):
+                        pkg.check(fn(m, n, k, A.data_ptr(), m, B.data_ptr(), n, C.data_ptr(), m, sh))
+                    one()
+                    ts = []
+                    for _ in range(max(5, min(args.steps, 9))):
+                        l2_flush()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        one()
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        ts.append(e0.elapsed_time(e1))
+                    ms = statistics.median(ts)
+                    rec[name] = {"gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), "config": pkg.tsm2_last_config()}
+                best = max(rec["tsm2r"]["gbs"], rec["tsm2l"]["gbs"])
+                rec["tsm2x_over_best"] = round(rec["tsm2x"]["gbs"] / best, 3)
+                worst = min(worst, rec["tsm2x_over_best"])
+                rows_x.append(rec)
+                del A, B, C
+        pkg.check(pkg.tsm2_get_device_status(sh))
+        crossover = {"workload": "binary32 A m x n (m in {15360, 2^20}, inner n in {4..1024}), B n x 16, "
+                                 "uniform[-1,1) seed 0; TSM2R vs TSM2L (B resident n <= 64, staged above) vs the "
+                                 "TSM2X choice", "worst_tsm2x_over_best": worst, "cases": rows_x}
+
     # ---- end to end through the C ABI with host buffers --------------------------------------
     # tsm2r_s_host / tsm2l_s_host: A, B, C in page-locked host memory; each
     # call streams A to the device in row chunks, overlapping copy-in, the
@@ -619,7 +659,7 @@ def run_gpu(args):
                    "step_wall_s": round(wall / args.steps, 4)},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
         "clocks": clock_rec, "fp64": fp64, "fwd_bwd": fwd_bwd, "mixed_precision": mixed, "batched": batched,
-        "cases": case_rows,
+        "crossover": crossover, "cases": case_rows,
         "src_hash": src_hash(),
     }
     if rank == 0:
@@ -682,6 +722,7 @@ def main():
     ap.add_argument("--no-fwdbwd", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-crossover", action="store_true")
     ap.add_argument("--case", default=None, help="op:dtype:m:n:k, e.g. r:f32:8192:8192:16 -- time one multiply only")
     args = ap.parse_args()
     if args.case:

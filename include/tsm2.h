@@ -147,6 +147,23 @@ tsm2_status tsm2r_bf16(int64_t m, int64_t n, int64_t k, const uint16_t *A_hi, co
 tsm2_status tsm2_split_bf16(int64_t rows, int64_t cols, const float *X, int64_t ldx,
                             uint16_t *hi, uint16_t *lo, int64_t ldh, void *stream);
 
+/* TSM2X: the same product, C = A B (tsm2r_* semantics, any n and k), with
+ * the schedule chosen from the shape: TSM2L (whole row blocks, B on chip or
+ * staged) for small inner dimensions on tall A, TSM2R (inner dimension split
+ * between blocks) otherwise.  The paper selects between its two kernels by
+ * the shape regime (Sec. 2.1, Sec. 3.2.1: TSM2R is latency-bound when the
+ * inner dimension is small); the thresholds here were measured on GB300:
+ * TSM2L when n <= tsm2x_choice's bound, i.e.
+ *   binary32: m >= 2^17: n <= 256; shorter A: n <= 64 (k <= 16), 128 (k > 16)
+ *   binary64: m >= 2^17: n <= 64 (k <= 16), 256 (k > 16); shorter: 32, 64. */
+tsm2_status tsm2x_s(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb,
+                    float *C, int64_t ldc, void *stream);
+tsm2_status tsm2x_d(int64_t m, int64_t n, int64_t k, const double *A, int64_t lda, const double *B, int64_t ldb,
+                    double *C, int64_t ldc, void *stream);
+/* The schedule tsm2x_s (elem_bytes 4) / tsm2x_d (8) runs for a shape: 'r' or
+ * 'l'; 0 for invalid arguments.  Host-only, no device call. */
+char tsm2x_choice(int elem_bytes, int64_t m, int64_t n, int64_t k);
+
 /* Host-resident operands: the same products with A, B and C in host memory
  * (page-locked memory gives full copy/compute overlap; pageable memory works
  * at lower speed).  The paper keeps its operands in device memory; these are

@@ -49,7 +49,7 @@ def _load():
             i64, vp, u64 = ctypes.c_int64, ctypes.c_void_p, ctypes.c_uint64
             gemm_sig = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]
             for name in ("tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s", "tsm2r_s_noalloc",
-                         "tsm2r_s_host", "tsm2r_d_host", "tsm2l_s_host", "tsm2l_d_host"):
+                         "tsm2r_s_host", "tsm2r_d_host", "tsm2l_s_host", "tsm2l_d_host", "tsm2x_s", "tsm2x_d", "tsm2x_choice", "tsm2x_s", "tsm2x_d"):
                 f = getattr(lib, name)
                 f.argtypes = gemm_sig
                 f.restype = ctypes.c_int
@@ -57,6 +57,8 @@ def _load():
                 f = getattr(lib, name)
                 f.argtypes = gemm_sig
                 f.restype = ctypes.c_int
+            lib.tsm2x_choice.argtypes = [ctypes.c_int, i64, i64, i64]
+            lib.tsm2x_choice.restype = ctypes.c_char
             lib.tsm2r_bf16.argtypes = [i64, i64, i64, vp, vp, i64, vp, i64, vp, i64, vp]
             lib.tsm2r_bf16.restype = ctypes.c_int
             lib.tsm2_split_bf16.argtypes = [i64, i64, vp, i64, vp, vp, i64, vp]
@@ -130,6 +132,20 @@ def tsm2l_s(m, n, k, A, lda, B, ldb, C, ldc, stream=0):
 
 def tsm2r_s_noalloc(m, n, k, A, lda, B, ldb, C, ldc, stream=0):
     return _load().tsm2r_s_noalloc(m, n, k, A, lda, B, ldb, C, ldc, stream)
+
+
+def tsm2x_s(m, n, k, A, lda, B, ldb, C, ldc, stream=0):
+    return _load().tsm2x_s(m, n, k, A, lda, B, ldb, C, ldc, stream)
+
+
+def tsm2x_d(m, n, k, A, lda, B, ldb, C, ldc, stream=0):
+    return _load().tsm2x_d(m, n, k, A, lda, B, ldb, C, ldc, stream)
+
+
+def tsm2x_choice(elem_bytes, m, n, k) -> str:
+    """'r' or 'l': the schedule tsm2x_s (4) / tsm2x_d (8) picks for the shape."""
+    c = _load().tsm2x_choice(elem_bytes, m, n, k)
+    return "" if c in (b"\x00", b"") else c.decode()
 
 
 def tsm2r_s_host(m, n, k, A, lda, B, ldb, C, ldc, stream=0):
@@ -301,7 +317,7 @@ def tsm2l(A, B, out=None):
 
 __all__ = [
     "tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s", "tsm2r_s_noalloc", "tsm2_get_last_error_string", "tsm2_last_config",
-    "tsm2r_s_host", "tsm2r_d_host", "tsm2l_s_host", "tsm2l_d_host",
+    "tsm2r_s_host", "tsm2r_d_host", "tsm2l_s_host", "tsm2l_d_host", "tsm2x_s", "tsm2x_d", "tsm2x_choice",
     "tsm2_get_device_status", "tsm2_shutdown", "tsm2_set_wait_budget_ns", "tsm2_set_path", "tsm2_set_grid", "tsm2_set_trace",
     "check", "tsm2r", "tsm2l", "tsm2r_t", "rankk", "empty_colmajor", "TSM2Error", "lib", "LIB_PATH",
     "tsm2r_t_d", "tsm2r_t_s", "tsm2_rankk_d", "tsm2_rankk_s", "tsm2r_bf16", "tsm2_split_bf16",

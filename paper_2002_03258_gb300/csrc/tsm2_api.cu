@@ -209,9 +209,6 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
                  const void *B, int64_t ldb, void *C, int64_t ldc, void *stream_v) {
     tsm2_status st = check_args(fn, m, n, k, A, lda, B, ldb, C, ldc, elem);
     if (st != TSM2_SUCCESS) return st;
-    if (op == 'l' && (n > 64 || k > 64))
-        return set_error(TSM2_ERR_UNSUPPORTED, "%s: TSM2L needs n <= 64 and k <= 64 (got n=%lld k=%lld)", fn,
-                         (long long)n, (long long)k);
     if (m == 0 || k == 0) {
         t_last_config = "empty";
         return TSM2_SUCCESS;
@@ -226,11 +223,14 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
     st = device_state(&dev);
     if (st != TSM2_SUCCESS) return st;
 
+    // TSM2L keeps B resident when n <= 64 and stages it with A otherwise
+    // (whole row blocks either way).
+    const bool staged_l = op == 'l' && n > 64;
     // The bulk-copy path needs 16-byte aligned bases and row strides, and
-    // 32-bit tensor coordinates.  The TSM2L schedule reads B with ordinary
-    // loads, so only A matters there.
+    // 32-bit tensor coordinates.  Resident B is read with ordinary loads, so
+    // only A matters there.
     const bool a_ok = aligned16(A) && ((lda * elem) % 16 == 0) && m < (1ll << 31) - 4096 && n < (1ll << 31);
-    const bool b_ok = op == 'l' || (aligned16(B) && ((ldb * elem) % 16 == 0));
+    const bool b_ok = (op == 'l' && !staged_l) || (aligned16(B) && ((ldb * elem) % 16 == 0));
     const bool use_stream = g_path != 1 && a_ok && b_ok;
 
     const int kc_max = use_stream ? (op == 'l' ? 32 : 16) : simple_kc_max();
@@ -254,8 +254,9 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
         }
         int kc = 2;
         while (kc < g.k) kc *= 2;
-        const StreamShape *shape = stream_shape(elem, op, kc);
-        if (op == 'l') {
+        if (staged_l && kc < 4) kc = 4;  // staged-B TSM2L: C columns in groups of four
+        const StreamShape *shape = stream_shape(elem, staged_l ? 't' : op, kc);
+        if (op == 'l' && !staged_l) {
             // Tall A: the 8-rows-per-lane schedule once every SM gets several
             // of its (larger) row blocks.
             const StreamShape *wide = stream_shape(elem, 'w', kc);
@@ -273,9 +274,10 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
         }
         const int64_t num_rb = (m + shape->BM - 1) / shape->BM;
         const int64_t upr = (n + shape->BNS - 1) / shape->BNS;
-        const int64_t ngroups = shape->b_resident ? num_rb : num_rb * upr;
+        const bool whole = shape->gran_rows == 0;  // row blocks never split: no partial sums
+        const int64_t ngroups = whole ? num_rb : num_rb * upr;
         int64_t grid = dev->sm_count;
-        if (!shape->b_resident) {
+        if (!whole) {
             // At least four stages per block so partial sums stay a small
             // fraction of the traffic.
             const int64_t cap = (num_rb * upr) / 4;
@@ -288,7 +290,7 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
         void *ws = nullptr;
         int *counters = nullptr;
         if (!shape->b_resident) {
-            const size_t slots = (size_t)(grid + num_rb) * shape->KC * shape->BM * elem;
+            const size_t slots = whole ? 0 : (size_t)(grid + num_rb) * shape->KC * shape->BM * elem;
             const size_t bt_off = (slots + 255) / 256 * 256;
             const size_t bt_bytes = shape->b_rowmajor ? (size_t)n * shape->KC * elem : 0;
             st = workspace(stream, (size_t)num_rb * sizeof(int), bt_off + bt_bytes, &ws, &counters);
@@ -781,6 +783,29 @@ tsm2_status gemm_r32_noalloc(int64_t m, int64_t n, int64_t k, const float *A, in
     return TSM2_SUCCESS;
 }
 
+// ---- TSM2X: choice between the TSM2R and TSM2L schedules --------------------
+//
+// TSM2R streams A in stages of 32 inner columns per row block of 256 (128)
+// rows and splits the inner dimension between blocks; with few inner columns
+// a row block is one or two stages long and the kernel is bound by latency
+// and per-row-block overheads (the paper's observation for small inner
+// dimensions, Sec. 3.2.1).  TSM2L owns whole, taller row blocks and keeps B
+// on chip (or stages it, n > 64); it needs enough row blocks to occupy the
+// GPU.  Largest n for which TSM2L was faster in a GB300 sweep over m in
+// {15360, 2^18, 2^20, 2^22, 2^23}, n in {2, 4, ..., 1024}, k in {16, 32}:
+//   binary32: m >= 2^17: n <= 256; shorter: n <= 64 (k <= 16), 128 (k > 16)
+//   binary64: m >= 2^17: n <= 64 (k <= 16), 256 (k > 16); shorter: 32, 64.
+int64_t tsm2x_l_max_n(int elem, int64_t m, int64_t k) {
+    const bool tall = m >= (int64_t(1) << 17);
+    const bool wide_c = k > 16;
+    if (elem == 4) return tall ? 256 : (wide_c ? 128 : 64);
+    return tall ? (wide_c ? 256 : 64) : (wide_c ? 64 : 32);
+}
+
+char tsm2x_schedule(int elem, int64_t m, int64_t n, int64_t k) {
+    return n <= tsm2x_l_max_n(elem, m, k) ? 'l' : 'r';
+}
+
 // ---- host-resident operands: row-chunk pipeline ---------------------------
 //
 // A is streamed to the device in chunks of whole rows (a 2-D copy: mc rows of
@@ -877,9 +902,6 @@ tsm2_status gemm_host(const char *fn, char op, int elem, int64_t m, int64_t n, i
                       const void *hB, int64_t ldb, void *hC, int64_t ldc, void *stream_v) {
     tsm2_status st = check_args(fn, m, n, k, hA, lda, hB, ldb, hC, ldc, elem);
     if (st != TSM2_SUCCESS) return st;
-    if (op == 'l' && (n > 64 || k > 64))
-        return set_error(TSM2_ERR_UNSUPPORTED, "%s: TSM2L needs n <= 64 and k <= 64 (got n=%lld k=%lld)", fn,
-                         (long long)n, (long long)k);
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     cudaError_t e;
     if (m == 0 || k == 0) {
@@ -1044,6 +1066,21 @@ void tsm2_shutdown(void) {
     }
     g_ws.clear();
     cudaSetDevice(cur);
+}
+
+tsm2_status tsm2x_s(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb, float *C,
+                    int64_t ldc, void *stream) {
+    return gemm("tsm2x_s", tsm2x_schedule(4, m, n, k), 4, m, n, k, A, lda, B, ldb, C, ldc, stream);
+}
+
+tsm2_status tsm2x_d(int64_t m, int64_t n, int64_t k, const double *A, int64_t lda, const double *B, int64_t ldb,
+                    double *C, int64_t ldc, void *stream) {
+    return gemm("tsm2x_d", tsm2x_schedule(8, m, n, k), 8, m, n, k, A, lda, B, ldb, C, ldc, stream);
+}
+
+char tsm2x_choice(int elem_bytes, int64_t m, int64_t n, int64_t k) {
+    if ((elem_bytes != 4 && elem_bytes != 8) || m < 0 || n < 0 || k < 0) return 0;
+    return tsm2x_schedule(elem_bytes, m, n, k);
 }
 
 tsm2_status tsm2r_s_host(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb,

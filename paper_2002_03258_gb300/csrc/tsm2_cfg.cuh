@@ -19,7 +19,7 @@ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
 
 template <typename T_, int KC_, int NV_, int WR_, int WC_, int WK_, int JW_, int STAGES_, bool BRES_, int NRES_,
-          bool BT_ = false, int BOXM_ = 0>
+          bool BT_ = false, int BOXM_ = 0, bool WHOLE_ = false>
 struct Cfg {
     using T = T_;
     using VT = Vec16<T>;
@@ -40,6 +40,10 @@ struct Cfg {
     // so packed FMAs pair C columns and duplicate the A value (R per inner
     // index) instead of the B value (KCW per inner index).
     static constexpr bool BT = BT_;
+    // Row blocks are never split between blocks (one group = one row block,
+    // no partial sums): always with resident B, optionally with streamed B
+    // (the TSM2L schedule for B too large to keep on chip).
+    static constexpr bool WHOLE = BRES_ || WHOLE_;
     static constexpr int R = NV * V;         // rows per lane
     static constexpr int BM = WR * 32 * R;   // rows per row block
     static constexpr int BNS = WC * JW;      // inner columns per stage
@@ -72,7 +76,8 @@ struct Cfg {
     static_assert(BM % BOXM == 0 && (32 * V) <= BOXM, "a warp's vector row group fits one box");
     static_assert(WC == 1 || (CC * BM) % NT == 0, "reduction rounds split evenly over threads");
     static_assert(!BRES || NRES % BNS == 0, "resident B covers whole stages");
-    static_assert(KC % WK == 0 && (WK == 1 || (WC == 1 && BRES)), "C columns split only in the TSM2L schedule");
+    static_assert(KC % WK == 0 && (WK == 1 || (WC == 1 && WHOLE)), "C columns split only in the TSM2L schedules");
+    static_assert(WC == 1 || !WHOLE, "whole row blocks need no cross-warp inner split");
     static_assert(SMEM <= 227 * 1024, "shared memory per block");
     static_assert(!BT || (sizeof(T) == 4 && KCW % 4 == 0), "row-major B: binary32, whole 16-byte column groups");
 };
@@ -248,5 +253,18 @@ constexpr WShape w32_shape(int kc) {
 template <int KC>
 using W32 = Cfg<float, KC, w32_shape(KC).nv, w32_shape(KC).wr, 1, w32_shape(KC).wk, w32_shape(KC).jw,
                 w32_shape(KC).st, true, 64, (TSM2_L_BT != 0 && (KC / w32_shape(KC).wk) % 4 == 0)>;
+
+// TSM2L with B staged instead of resident (Alg. 6's setting, Sec. 3.2.2: B
+// too large to stay on chip, here n > 64): B rows arrive with each A stage,
+// but every block still owns whole row blocks and keeps their C columns in
+// registers across the inner loop, so C is written once and A is read once
+// per 32 columns of C.  Shapes of the resident schedules with 8 inner columns
+// per stage (three 64 KiB stages for the 2048-row blocks of KC <= 8); C
+// columns in groups of at least four (narrower k pads to KC = 4).
+template <int KC>
+using T32 = Cfg<float, KC, w32_shape(KC).nv, w32_shape(KC).wr, 1, w32_shape(KC).wk, 8, (KC <= 8 ? 3 : w32_shape(KC).st),
+                false, 0, ((KC / w32_shape(KC).wk) % 4 == 0), 0, true>;
+template <int KC>
+using T64 = Cfg<double, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, 5, false, 0, false, 0, true>;
 
 }  // namespace tsm2

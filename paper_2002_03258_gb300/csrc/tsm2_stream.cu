@@ -235,7 +235,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             const int64_t rb64 = rb;
             const int64_t rb_u0 = rb64 * p.upr;
             // TSM2L runs are whole row blocks by construction (gran = upr).
-            const bool whole = K::BRES || (piece_at_rb_start && rb_end);
+            const bool whole = K::WHOLE || (piece_at_rb_start && rb_end);
             const int64_t row0 = rb64 * K::BM;
             T *C = static_cast<T *>(p.C);
             T *ws = static_cast<T *>(p.ws);
@@ -279,7 +279,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                             }
                         }
                     }
-                } else if constexpr (!K::BRES) {
+                } else if constexpr (!K::WHOLE) {
                     // Partial sums in registers -> slot [KC][BM] at this lane's rows.
                     T *slot = ws + my_slot * (int64_t)(K::KC * K::BM);
 #pragma unroll
@@ -328,7 +328,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                 }
             }
 
-            if (!K::BRES && !whole) {
+            if (!K::WHOLE && !whole) {
                 // Publish this piece; the last arriving block of the row block
                 // adds all pieces in block order and writes C.
                 __threadfence();
@@ -434,7 +434,7 @@ cudaError_t launch_cfg(const StreamLaunch &L, cudaStream_t stream) {
     p.wait_ns = L.wait_ns;
     const int64_t num_rb = (L.g.m + K::BM - 1) / K::BM;
     p.upr = (L.g.n + K::BNS - 1) / K::BNS;
-    p.gran = K::BRES ? p.upr : 1;  // TSM2L schedule keeps row blocks whole
+    p.gran = K::WHOLE ? p.upr : 1;  // TSM2L schedules keep row blocks whole
     p.ngroups = num_rb * p.upr / p.gran;
     p.c_vec = L.c_vec ? 1 : 0;
     p.trace = L.trace;
@@ -451,7 +451,7 @@ StreamShape shape_of(const char *name) {
     s.BM = K::BM;
     s.BNS = K::BNS;
     s.BOXM = K::BOXM;
-    s.gran_rows = K::BRES ? 0 : 1;
+    s.gran_rows = K::WHOLE ? 0 : 1;
     s.b_resident = K::BRES;
     s.b_rowmajor = K::BT && !K::BRES;
     s.n_max_resident = K::NRES;
@@ -461,7 +461,7 @@ StreamShape shape_of(const char *name) {
 }
 
 struct Entry {
-    char op;  // 'r': TSM2R schedule, 'l': TSM2L, 'w': TSM2L with 8 rows per lane
+    char op;  // 'r': TSM2R schedule, 'l': TSM2L, 'w': TSM2L with 8 rows per lane, 't': TSM2L with staged B
     StreamShape shape;
     cudaError_t (*launch)(const StreamLaunch &, cudaStream_t);
 };
@@ -481,6 +481,10 @@ const Entry kEntries[] = {
     TSM2_ENTRY('w', W32<2>, "lw_f32_kc2"),  TSM2_ENTRY('w', W32<4>, "lw_f32_kc4"),
     TSM2_ENTRY('w', W32<8>, "lw_f32_kc8"),  TSM2_ENTRY('w', W32<16>, "lw_f32_kc16"),
     TSM2_ENTRY('w', W32<32>, "lw_f32_kc32"),
+    TSM2_ENTRY('t', T32<4>, "lt_f32_kc4"),  TSM2_ENTRY('t', T32<8>, "lt_f32_kc8"),
+    TSM2_ENTRY('t', T32<16>, "lt_f32_kc16"), TSM2_ENTRY('t', T32<32>, "lt_f32_kc32"),
+    TSM2_ENTRY('t', T64<4>, "lt_f64_kc4"),  TSM2_ENTRY('t', T64<8>, "lt_f64_kc8"),
+    TSM2_ENTRY('t', T64<16>, "lt_f64_kc16"), TSM2_ENTRY('t', T64<32>, "lt_f64_kc32"),
 };
 
 }  // namespace

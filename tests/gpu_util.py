@@ -7,7 +7,8 @@ import oracle
 
 DT = {np.float64: torch.float64, np.float32: torch.float32}
 FN = {("r", np.float64): "tsm2r_d", ("r", np.float32): "tsm2r_s",
-      ("l", np.float64): "tsm2l_d", ("l", np.float32): "tsm2l_s"}
+      ("l", np.float64): "tsm2l_d", ("l", np.float32): "tsm2l_s",
+      ("x", np.float64): "tsm2x_d", ("x", np.float32): "tsm2x_s"}
 
 
 class DevMat:

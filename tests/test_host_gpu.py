@@ -120,5 +120,6 @@ def test_host_entry_edge_cases():
     assert pkg.tsm2r_s_host(0, 4, 3, tA.data_ptr(), 1, tA.data_ptr(), 4, tC.data_ptr(), 1, 0) == 0
     assert pkg.tsm2r_s_host(10, 4, 0, tA.data_ptr(), 10, tA.data_ptr(), 4, tC.data_ptr(), 10, 0) == 0
     assert np.all(tC.numpy() == 5.0)
-    # TSM2L with n > 64 is unsupported
-    assert pkg.tsm2l_s_host(10, 65, 3, tA.data_ptr(), 10, tA.data_ptr(), 65, tC.data_ptr(), 10, 0) == pkg.ERR_UNSUPPORTED
+    # TSM2L with n > 64: B staged with A
+    C, A, B = run_host("l", np.float32, 50000, 100, 20)
+    assert_parity(C, A, B, np.float32)
