@@ -61,15 +61,29 @@ def alg_bytes(m, n, k, es):
     return es * (m * n + n * k + m * k)
 
 
-def launches_per_call(op, k):
+def launches_per_call(op, n, k):
+    """Kernels one tsm2r_s / tsm2l_s call launches (binary32, bulk-copy path):
+    one per column chunk (16 for TSM2R, 32 for TSM2L), plus the B packing
+    kernel before each chunk that reads B row-major (TSM2R chunks of 9..16
+    columns; staged-B TSM2L, n > 64)."""
     kc = 32 if op == "l" else 16
-    return (k + kc - 1) // kc
+    total = 0
+    for c0 in range(0, k, kc):
+        kk = min(kc, k - c0)
+        packs = (op == "r" and kk > 8) or (op == "l" and n > 64)
+        total += 1 + int(packs)
+    return total
+
+
+# Sources that define and launch the bulk-copy kernels (the dominant kernel's
+# DRAM-traffic record is tied to these).
+KERNEL_SOURCES = ("common.cuh", "internal.h", "tsm2_api.cu", "tsm2_cfg.cuh", "tsm2_stream.cu")
 
 
 def src_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2002_03258_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -334,6 +348,53 @@ def run_gpu(args):
                 "kernel": configs.get(dom), "workload": wkey, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": dw["bytes"]}
 
+    # ---- end to end through the C ABI with host buffers --------------------------------------
+    # tsm2r_s_host / tsm2l_s_host: A, B, C in page-locked host memory; each
+    # call streams A to the device in row chunks, overlapping copy-in, the
+    # product and the copy-out of C (all inside the timed region).
+    h_in, h_out, h_shared = [], [], {}
+    for w in work32:
+        key = w["A"].data_ptr()  # cases that share a device A share its host copy
+        if key not in h_shared:
+            h_shared[key] = torch.empty((w["n"], w["m"]), dtype=w["A"].dtype, pin_memory=True).t()
+            h_shared[key].copy_(w["A"])
+        hA = h_shared[key]
+        hB = torch.empty((w["k"], w["n"]), dtype=w["A"].dtype, pin_memory=True).t()
+        hB.copy_(w["B"][:, :w["k"]])
+        hC = torch.empty((w["k"], w["m"]), dtype=w["A"].dtype, pin_memory=True).t()
+        h_in.append((hA, hB))
+        h_out.append(hC)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 5))
+    h2d = sum(w["A"].numel() * w["es"] + w["n"] * w["k"] * w["es"] for w in work32)
+    d2h = sum(w["m"] * w["k"] * w["es"] for w in work32)
+    host_fn = {"r": pkg.tsm2r_s_host, "l": pkg.tsm2l_s_host}
+
+    def e2e_step():
+        for (hA, hB), hC, w in zip(h_in, h_out, work32):
+            pkg.check(host_fn[w["op"]](w["m"], w["n"], w["k"], hA.data_ptr(), w["m"], hB.data_ptr(), w["n"],
+                                       hC.data_ptr(), w["m"], sh))
+
+    e2e_step()  # staging buffers allocated outside the timed region
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_start.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e_start.elapsed_time(e_end) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": round(world * step_bytes / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)}
+    del h_in, h_out, h_shared
+
     # ---- cuBLAS comparator on the same operands (not timed in the step) -----------------
     cublas = []
     if not args.no_cublas:
@@ -596,59 +657,13 @@ def run_gpu(args):
                                  "uniform[-1,1) seed 0; TSM2R vs TSM2L (B resident n <= 64, staged above) vs the "
                                  "TSM2X choice", "worst_tsm2x_over_best": worst, "cases": rows_x}
 
-    # ---- end to end through the C ABI with host buffers --------------------------------------
-    # tsm2r_s_host / tsm2l_s_host: A, B, C in page-locked host memory; each
-    # call streams A to the device in row chunks, overlapping copy-in, the
-    # product and the copy-out of C (all inside the timed region).
-    h_in, h_out, h_shared = [], [], {}
-    for w in work32:
-        key = w["A"].data_ptr()  # cases that share a device A share its host copy
-        if key not in h_shared:
-            h_shared[key] = torch.empty((w["n"], w["m"]), dtype=w["A"].dtype, pin_memory=True).t()
-            h_shared[key].copy_(w["A"])
-        hA = h_shared[key]
-        hB = torch.empty((w["k"], w["n"]), dtype=w["A"].dtype, pin_memory=True).t()
-        hB.copy_(w["B"][:, :w["k"]])
-        hC = torch.empty((w["k"], w["m"]), dtype=w["A"].dtype, pin_memory=True).t()
-        h_in.append((hA, hB))
-        h_out.append(hC)
-    torch.cuda.synchronize()
-    e2e_steps = max(1, min(args.steps, 5))
-    h2d = sum(w["A"].numel() * w["es"] + w["n"] * w["k"] * w["es"] for w in work32)
-    d2h = sum(w["m"] * w["k"] * w["es"] for w in work32)
-    host_fn = {"r": pkg.tsm2r_s_host, "l": pkg.tsm2l_s_host}
-
-    def e2e_step():
-        for (hA, hB), hC, w in zip(h_in, h_out, work32):
-            pkg.check(host_fn[w["op"]](w["m"], w["n"], w["k"], hA.data_ptr(), w["m"], hB.data_ptr(), w["n"],
-                                       hC.data_ptr(), w["m"], sh))
-
-    e2e_step()  # staging buffers allocated outside the timed region
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e_start.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
-    e_end.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e_start.elapsed_time(e_end) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": round(world * step_bytes / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)}
-
     # ---- CPU oracle baseline (rank 0, N = 1) --------------------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, desc, cores, _ = oracle_sample_run("f32", 1, 0)
         cpu = {"value": round(v, 4), "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc}
 
-    n_launch = args.steps * sum(launches_per_call(w["op"], w["k"]) for w in work32)
+    n_launch = args.steps * sum(launches_per_call(w["op"], w["n"], w["k"]) for w in work32)
     line = {
         "metric": "TSM2R/TSM2L achieved HBM GB/s (binary32 sweep)", "value": round(value, 2), "unit": "GB/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(mean_step_ms, 4),
@@ -679,9 +694,12 @@ def run_case(args):
     import tsm2_inputs as ti
     op, dt, m, n, k = args.case.split(":")
     m, n, k = int(m), int(n), int(k)
-    tdt = torch.float32 if dt == "f32" else torch.float64
-    suf = "s" if dt == "f32" else "d"
-    es = 4 if dt == "f32" else 8
+    bf16 = dt in ("bf16", "bf16hilo")  # TSM2R with A in bfloat16 (hi, or hi + lo), B and C binary32
+    if bf16 and op != "r":
+        raise SystemExit("bfloat16 A is a TSM2R variant: use op r")
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    suf = "d" if dt == "f64" else "s"
+    es = 8 if dt == "f64" else 4
     lib = pkg.lib()
     A = torch.empty((n, m), dtype=tdt, device="cuda").t()
     B = torch.empty((k, n), dtype=tdt, device="cuda").t()
@@ -689,15 +707,31 @@ def run_case(args):
     fill = getattr(lib, f"tsm2_fill_uniform_{suf}")
     pkg.check(fill(m, n, 0, ti.MID_A, A.data_ptr(), m, 0))
     pkg.check(fill(n, k, 0, ti.MID_B, B.data_ptr(), n, 0))
+    if bf16:
+        hi = torch.empty((n, m), dtype=torch.int16, device="cuda")
+        lo = torch.empty((n, m), dtype=torch.int16, device="cuda") if dt == "bf16hilo" else None
+        pkg.check(pkg.tsm2_split_bf16(m, n, A.data_ptr(), m, hi.data_ptr(), lo.data_ptr() if lo is not None else None,
+                                      m, 0))
+        del A
+        es_a = 4 if dt == "bf16hilo" else 2
+
+        def fn(m_, n_, k_, _a, lda, b, ldb, c, ldc, st):
+            return pkg.tsm2r_bf16(m_, n_, k_, hi.data_ptr(), lo.data_ptr() if lo is not None else None, lda, b, ldb,
+                                  c, ldc, st)
+        A_ptr = 0
+        nbytes = es_a * m * n + 4 * (n * k + m * k)
+    else:
+        fn = getattr(pkg, f"tsm2{op}_{suf}")
+        A_ptr = A.data_ptr()
+        nbytes = alg_bytes(m, n, k, es)
     l2 = getattr(torch.cuda.get_device_properties(0), "L2_cache_size", 128 << 20) or (128 << 20)
     flush = torch.empty(2 * l2, dtype=torch.uint8, device="cuda")
-    fn = getattr(pkg, f"tsm2{op}_{suf}")
     ts = []
     for r in range(args.warmup + args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        pkg.check(fn(m, n, k, A.data_ptr(), m, B.data_ptr(), n, C.data_ptr(), m, 0))
+        pkg.check(fn(m, n, k, A_ptr, m, B.data_ptr(), n, C.data_ptr(), m, 0))
         e1.record()
         torch.cuda.synchronize()
         if r >= args.warmup:
@@ -705,8 +739,8 @@ def run_case(args):
     pkg.check(pkg.tsm2_get_device_status(0))
     ms = statistics.median(ts)
     print(json.dumps({"case": args.case, "config": pkg.tsm2_last_config(), "ms": round(ms, 4),
-                      "gbs": round(alg_bytes(m, n, k, es) / (ms * 1e-3) / 1e9, 1),
-                      "algorithmic_bytes": alg_bytes(m, n, k, es), "src_hash": src_hash()}), flush=True)
+                      "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                      "algorithmic_bytes": nbytes, "src_hash": src_hash()}), flush=True)
     return 0
 
 
@@ -723,7 +757,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-crossover", action="store_true")
-    ap.add_argument("--case", default=None, help="op:dtype:m:n:k, e.g. r:f32:8192:8192:16 -- time one multiply only")
+    ap.add_argument("--case", default=None, help="op:dtype:m:n:k, e.g. r:f32:8192:8192:16 -- time one multiply only (op r, l or x; dtype "
+                         "f32, f64, or for op r bf16 / bf16hilo)")
     args = ap.parse_args()
     if args.case:
         return run_case(args)

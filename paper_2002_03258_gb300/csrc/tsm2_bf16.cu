@@ -21,14 +21,17 @@
 //        hi+lo:  C += Ahi*(B1+B2+B3) + Alo*(B1+B2) (drops only Alo*B3,
 //                                                   < 2^-26 |A||B| per product)
 //    tcgen05.commit releases each shared-memory stage back to the producer.
-//  * Each stage's MMAs accumulate into one of four TMEM buffers (4 x 64
-//    columns: 16 per row tile, so the MMAs can run stages ahead of the drain); four epilogue warps drain it with tcgen05.ld after every stage
-//    (one TMEM lane = one row of C) and carry the sum over stages in
-//    registers with round-to-nearest binary32 adds -- the tensor cores' own
-//    accumulation is then used for 4 (plain) or 20 (hi+lo) products' worth of
-//    partial sums only, which keeps hi+lo at binary32-like accuracy.  Pieces
-//    end in C, or in a partial sum for the same deterministic stream-K fix-up
-//    as the CUDA-core kernels.
+//  * A group of stages accumulates into one of four TMEM buffers (4 x 64
+//    columns: 16 per row tile, so the MMAs can run groups ahead of the
+//    drain); four epilogue warps drain it with tcgen05.ld after every group
+//    (one TMEM lane = one row of C, the four row tiles' loads in flight
+//    together) and carry the sum over groups in registers with
+//    round-to-nearest binary32 adds.  hi+lo drains after every stage (the
+//    tensor cores' own accumulation then covers 20 products' worth of
+//    partial sums only, which keeps hi+lo at binary32-like accuracy); plain
+//    drains every 8 stages, far below its bfloat16 representation error.
+//    Groups never cross a row block.  Pieces end in C, or in a partial sum
+//    for the same deterministic stream-K fix-up as the CUDA-core kernels.
 // Every wait is bounded; TMEM is always released before the block exits.
 #include "common.cuh"
 #include "internal.h"
@@ -99,17 +102,18 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// 16 consecutive TMEM columns of this warp's 32 lanes; the caller waits
+// (tmem_ld_wait) before using the registers, so several loads can be in
+// flight at once.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -131,6 +135,7 @@ struct BParams {
     int64_t upr;     // stages per row block
     int64_t ngroups; // units in total
     int hilo;
+    int group;        // stages summed in TMEM per drain (1 for hi+lo)
     int stages;       // ring depth
     int stage_bytes;  // ring stride (A_hi, [A_lo], B pieces)
 };
@@ -227,12 +232,19 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
             uint32_t ph = 0;
             uint32_t acc_ph = 0;  // bit b: parity of buffer b
             int buf = 0;
+            int gcnt = 0;         // stages already summed into the current buffer
+            int kc = (int)(u_begin % p.upr);
             bool issued_any = false;
             for (int i = 0; i < nunits; ++i) {
                 if (flags[0]) break;
-                // Each stage accumulates into its own TMEM buffer, which the
-                // epilogue must have drained (two buffers alternate).
-                if (!mbar_wait_bounded(&acce[buf], ((acc_ph >> buf) & 1u) ^ 1u, p.wait_ns, flags)) {
+                // Each group of stages accumulates into its own TMEM buffer,
+                // which the epilogue must have drained (four buffers rotate).
+                // A group ends after p.group stages, at the end of a row
+                // block and at the block's last unit (the epilogue tracks the
+                // same boundaries).
+                const bool gstart = (gcnt == 0);
+                const bool gend = (gcnt + 1 == p.group) || (kc == upr - 1) || (i == nunits - 1);
+                if (gstart && !mbar_wait_bounded(&acce[buf], ((acc_ph >> buf) & 1u) ^ 1u, p.wait_ns, flags)) {
                     flags[0] = 1;
                     atomicOr(p.status, kStatusTimeout);
                     break;
@@ -260,7 +272,7 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
                         const uint64_t ahi = sdesc(st + aoff, kBox, 1024, 2);
                         const uint64_t alo = sdesc(st + kATile + aoff, kBox, 1024, 2);
                         const uint32_t d = tmem + (uint32_t)(buf * kBufCols + sub * kKC);
-                        umma_f16(d, ahi, b1, ks == 0 ? 0u : 1u);
+                        umma_f16(d, ahi, b1, (gstart && ks == 0) ? 0u : 1u);
                         umma_f16(d, ahi, b2, 1u);
                         if (p.hilo) {
                             umma_f16(d, ahi, b3, 1u);
@@ -270,11 +282,17 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
                     }
                 }
                 issued_any = true;
-                umma_commit(&empty[s]);     // stage s may be refilled once these MMAs are done
-                umma_commit(&accf[buf]);    // and this stage's sum is ready for the epilogue
-                acc_ph ^= 1u << buf;
-                if (++buf == kNBuf) buf = 0;
+                umma_commit(&empty[s]);  // stage s may be refilled once these MMAs are done
+                if (gend) {
+                    umma_commit(&accf[buf]);  // and the group's sum is ready for the epilogue
+                    acc_ph ^= 1u << buf;
+                    if (++buf == kNBuf) buf = 0;
+                    gcnt = 0;
+                } else {
+                    ++gcnt;
+                }
                 if (++s == nst) { s = 0; ph ^= 1u; }
+                if (++kc == upr) kc = 0;
             }
             // Every MMA this thread issued has completed before TMEM is freed.
             if (issued_any) {
@@ -300,34 +318,45 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
         for (int sub = 0; sub < kSub; ++sub)
 #pragma unroll
             for (int c = 0; c < kKC; ++c) v[sub][c] = 0.f;
+        int gcnt = 0;
         for (int i = 0; i < nunits; ++i) {
             const bool rb_end = (kc == upr - 1);
-            if (!aborted) {
-                bool ok = !flags[0] && mbar_wait_bounded(&accf[buf], (acc_ph >> buf) & 1u, p.wait_ns, flags);
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) {
-                    aborted = true;
-                    if (lane == 0) {
-                        flags[0] = 1;
-                        atomicOr(p.status, kStatusTimeout);
+            const bool gend = (gcnt + 1 == p.group) || rb_end || (i == nunits - 1);
+            if (gend) {
+                if (!aborted) {
+                    bool ok = !flags[0] && mbar_wait_bounded(&accf[buf], (acc_ph >> buf) & 1u, p.wait_ns, flags);
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok) {
+                        aborted = true;
+                        if (lane == 0) {
+                            flags[0] = 1;
+                            atomicOr(p.status, kStatusTimeout);
+                        }
                     }
                 }
-            }
-            if (!aborted) {
-                tc_fence_after();
+                if (!aborted) {
+                    tc_fence_after();
+                    // All four row tiles' loads in flight together, one wait.
+                    uint32_t t[kSub][16];
 #pragma unroll
-                for (int sub = 0; sub < kSub; ++sub) {
-                    float t[16];
-                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * kBufCols + sub * kKC), t);
+                    for (int sub = 0; sub < kSub; ++sub)
+                        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * kBufCols + sub * kKC),
+                                  t[sub]);
+                    tmem_ld_wait();
 #pragma unroll
-                    for (int c = 0; c < kKC; ++c) v[sub][c] += t[c];
+                    for (int sub = 0; sub < kSub; ++sub)
+#pragma unroll
+                        for (int c = 0; c < kKC; ++c) v[sub][c] += __uint_as_float(t[sub][c]);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acce[buf]);
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acce[buf]);
+                acc_ph ^= 1u << buf;
+                if (++buf == kNBuf) buf = 0;
+                gcnt = 0;
+            } else {
+                ++gcnt;
             }
-            acc_ph ^= 1u << buf;
-            if (++buf == kNBuf) buf = 0;
             if (rb_end || i == nunits - 1) {
                 const bool whole = piece_at_start && rb_end;
                 const int64_t rb64 = rb;
@@ -521,6 +550,10 @@ cudaError_t bf16_launch(const BF16Launch &L, cudaStream_t stream) {
     p.upr = (L.n + kBK - 1) / kBK;
     p.ngroups = ((L.m + kBM - 1) / kBM) * p.upr;
     p.hilo = L.hilo ? 1 : 0;
+    // Plain: the tensor cores sum 8 stages (512 products per output) before
+    // each drain, far inside the bfloat16 representation error of A; hi+lo:
+    // one stage per drain, for binary32-like accuracy.
+    p.group = L.hilo ? 1 : 8;
     p.stage_bytes = L.hilo ? kStageHiLo : kStagePlain;
     p.stages = kSmemBudget / p.stage_bytes;
     if (p.stages > kMaxStages) p.stages = kMaxStages;

@@ -237,18 +237,13 @@ template <int KC> using L64 = Cfg<double, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 3
 // FMAs; the C columns are split over WK = 1, 2, 4 warps (KC <= 8, 16, 32) so a
 // lane never holds more than 64 accumulators.  Chosen when there are enough
 // row blocks for an even spread over the SMs.
-#ifndef TSM2_W32_VAR
-#define TSM2_W32_VAR 0
-#endif
 struct WShape {
     int nv, wr, wk, jw, st;
 };
+// (Shapes with 128 accumulators per lane -- WK = 2 for KC = 32, WK = 1 for
+// KC = 16 -- spill several hundred bytes in this kernel and are not used.)
 constexpr WShape w32_shape(int kc) {
-    return kc >= 32 ? (TSM2_W32_VAR == 1   ? WShape{2, 4, 2, 8, 5}
-                       : TSM2_W32_VAR == 2 ? WShape{4, 2, 4, 8, 5}
-                                           : WShape{2, 2, 4, 8, 5})
-         : kc >= 16 ? (TSM2_W32_VAR == 1 ? WShape{2, 8, 1, 8, 3} : WShape{2, 4, 2, 8, 5})
-                    : WShape{2, 8, 1, 4, 5};
+    return kc >= 32 ? WShape{2, 2, 4, 8, 5} : kc >= 16 ? WShape{2, 4, 2, 8, 5} : WShape{2, 8, 1, 4, 5};
 }
 template <int KC>
 using W32 = Cfg<float, KC, w32_shape(KC).nv, w32_shape(KC).wr, 1, w32_shape(KC).wk, w32_shape(KC).jw,
@@ -259,11 +254,12 @@ using W32 = Cfg<float, KC, w32_shape(KC).nv, w32_shape(KC).wr, 1, w32_shape(KC).
 // but every block still owns whole row blocks and keeps their C columns in
 // registers across the inner loop, so C is written once and A is read once
 // per 32 columns of C.  Shapes of the resident schedules with 8 inner columns
-// per stage (three 64 KiB stages for the 2048-row blocks of KC <= 8); C
+// per stage (three 64 KiB stages for 2048-row blocks); C
 // columns in groups of at least four (narrower k pads to KC = 4).
 template <int KC>
-using T32 = Cfg<float, KC, w32_shape(KC).nv, w32_shape(KC).wr, 1, w32_shape(KC).wk, 8, (KC <= 8 ? 3 : w32_shape(KC).st),
-                false, 0, ((KC / w32_shape(KC).wk) % 4 == 0), 0, true>;
+using T32 = Cfg<float, KC, w32_shape(KC).nv, w32_shape(KC).wr, 1, w32_shape(KC).wk, 8,
+                (w32_shape(KC).wr * w32_shape(KC).nv >= 16 ? 3 : w32_shape(KC).st), false, 0,
+                ((KC / w32_shape(KC).wk) % 4 == 0), 0, true>;
 template <int KC>
 using T64 = Cfg<double, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, 5, false, 0, false, 0, true>;
 
