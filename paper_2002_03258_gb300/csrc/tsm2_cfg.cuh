@@ -19,7 +19,7 @@ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
 
 template <typename T_, int KC_, int NV_, int WR_, int WC_, int WK_, int JW_, int STAGES_, bool BRES_, int NRES_,
-          bool BT_ = false, int BOXM_ = 0, bool WHOLE_ = false>
+          bool BT_ = false, int BOXM_ = 0, bool WHOLE_ = false, bool SEPI_ = false>
 struct Cfg {
     using T = T_;
     using VT = Vec16<T>;
@@ -44,6 +44,10 @@ struct Cfg {
     // no partial sums): always with resident B, optionally with streamed B
     // (the TSM2L schedule for B too large to keep on chip).
     static constexpr bool WHOLE = BRES_ || WHOLE_;
+    // Whole row blocks write C through shared memory (rounds of CC columns
+    // of every column-warp group, then coalesced copies): storing 128
+    // accumulators straight from registers costs spills in this kernel.
+    static constexpr bool SEPI = SEPI_;
     static constexpr int R = NV * V;         // rows per lane
     static constexpr int BM = WR * 32 * R;   // rows per row block
     static constexpr int BNS = WC * JW;      // inner columns per stage
@@ -58,7 +62,7 @@ struct Cfg {
     static constexpr int CQ = cmin(KCW, TSM2_CQ);  // C columns per group of the inner loop
     static constexpr int A_STAGE = BM * BNS;                 // elements
     static constexpr int B_STAGE = BRES ? 0 : BNS * KC;      // elements
-    static constexpr int RED = WC > 1 ? WC * CC * BM : 0;    // elements
+    static constexpr int RED = WC > 1 ? WC * CC * BM : (SEPI ? WK * CC * BM : 0);  // elements
     static constexpr int BRES_ELEMS = BRES ? KC * NRES : 0;  // elements
     static constexpr uint32_t TX_BYTES = (uint32_t)((A_STAGE + B_STAGE) * sizeof(T));
     static constexpr size_t OFF_A = 0;
@@ -78,6 +82,8 @@ struct Cfg {
     static_assert(!BRES || NRES % BNS == 0, "resident B covers whole stages");
     static_assert(KC % WK == 0 && (WK == 1 || (WC == 1 && WHOLE)), "C columns split only in the TSM2L schedules");
     static_assert(WC == 1 || !WHOLE, "whole row blocks need no cross-warp inner split");
+    static_assert(!SEPI || (WHOLE && WC == 1 && KCW % CC == 0 && (WK * CC * BM) % (4 * NT) == 0 && BM % 4 == 0),
+                  "staged epilogue: whole row blocks, column rounds of CC, whole 16-byte vectors per thread");
     static_assert(SMEM <= 227 * 1024, "shared memory per block");
     static_assert(!BT || (sizeof(T) == 4 && KCW % 4 == 0), "row-major B: binary32, whole 16-byte column groups");
 };
@@ -237,29 +243,43 @@ template <int KC> using L64 = Cfg<double, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 3
 // FMAs; the C columns are split over WK = 1, 2, 4 warps (KC <= 8, 16, 32) so a
 // lane never holds more than 64 accumulators.  Chosen when there are enough
 // row blocks for an even spread over the SMs.
+// KC = 16 keeps 16 C columns per lane (128 accumulators, WK = 1), so each A
+// value read from shared memory feeds 16 columns instead of 8; C then goes
+// out through shared memory (SEPI).  For KC = 32 the same width (WK = 2)
+// measured slower with resident B: its row blocks are 4 stages long and the
+// staged C copy stalls the warps that compute; 8 columns per lane stay.
 struct WShape {
     int nv, wr, wk, jw, st;
+    bool sepi;
 };
-// (Shapes with 128 accumulators per lane -- WK = 2 for KC = 32, WK = 1 for
-// KC = 16 -- spill several hundred bytes in this kernel and are not used.)
 constexpr WShape w32_shape(int kc) {
-    return kc >= 32 ? WShape{2, 2, 4, 8, 5} : kc >= 16 ? WShape{2, 4, 2, 8, 5} : WShape{2, 8, 1, 4, 5};
+    return kc >= 32 ? WShape{2, 2, 4, 8, 5, false} : kc >= 16 ? WShape{2, 8, 1, 4, 5, true} : WShape{2, 8, 1, 4, 5, false};
 }
 template <int KC>
 using W32 = Cfg<float, KC, w32_shape(KC).nv, w32_shape(KC).wr, 1, w32_shape(KC).wk, w32_shape(KC).jw,
-                w32_shape(KC).st, true, 64, (TSM2_L_BT != 0 && (KC / w32_shape(KC).wk) % 4 == 0)>;
+                w32_shape(KC).st, true, 64, (TSM2_L_BT != 0 && (KC / w32_shape(KC).wk) % 4 == 0), 0, false,
+                w32_shape(KC).sepi>;
+// The batched kernel writes C straight from registers: 8 C columns per lane.
+constexpr WShape w32n_shape(int kc) {
+    return kc >= 32 ? WShape{2, 2, 4, 8, 5, false} : kc >= 16 ? WShape{2, 4, 2, 8, 5, false} : WShape{2, 8, 1, 4, 5, false};
+}
+template <int KC>
+using W32N = Cfg<float, KC, w32n_shape(KC).nv, w32n_shape(KC).wr, 1, w32n_shape(KC).wk, w32n_shape(KC).jw,
+                 w32n_shape(KC).st, true, 64, (TSM2_L_BT != 0 && (KC / w32n_shape(KC).wk) % 4 == 0)>;
 
 // TSM2L with B staged instead of resident (Alg. 6's setting, Sec. 3.2.2: B
 // too large to stay on chip, here n > 64): B rows arrive with each A stage,
 // but every block still owns whole row blocks and keeps their C columns in
 // registers across the inner loop, so C is written once and A is read once
-// per 32 columns of C.  Shapes of the resident schedules with 8 inner columns
-// per stage (three 64 KiB stages for 2048-row blocks); C
-// columns in groups of at least four (narrower k pads to KC = 4).
+// per 32 columns of C.  16 C columns per lane for KC >= 16 (C staged through
+// shared memory), 8 inner columns per stage for KC = 32; C columns in groups
+// of at least four (narrower k pads to KC = 4).
+constexpr WShape t32_shape(int kc) {
+    return kc >= 32 ? WShape{2, 4, 2, 8, 5, true} : kc >= 16 ? WShape{2, 8, 1, 4, 4, true} : WShape{2, 8, 1, 8, 3, false};
+}
 template <int KC>
-using T32 = Cfg<float, KC, w32_shape(KC).nv, w32_shape(KC).wr, 1, w32_shape(KC).wk, 8,
-                (w32_shape(KC).wr * w32_shape(KC).nv >= 16 ? 3 : w32_shape(KC).st), false, 0,
-                ((KC / w32_shape(KC).wk) % 4 == 0), 0, true>;
+using T32 = Cfg<float, KC, t32_shape(KC).nv, t32_shape(KC).wr, 1, t32_shape(KC).wk, t32_shape(KC).jw, t32_shape(KC).st,
+                false, 0, ((KC / t32_shape(KC).wk) % 4 == 0), 0, true, t32_shape(KC).sepi>;
 template <int KC>
 using T64 = Cfg<double, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, 5, false, 0, false, 0, true>;
 

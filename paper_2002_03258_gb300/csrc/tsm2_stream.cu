@@ -245,7 +245,55 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             const int64_t my_slot = g + rb64;
             const int tid = threadIdx.x - 128;  // 0 .. NT-1 for consumers
 
-            if constexpr (K::WC == 1) {
+            if constexpr (K::SEPI) {
+                // Whole row block, C through shared memory: for each round of
+                // CC of its columns, every warp stores them at its rows of
+                // sRed (slot wk*CC + cc); then all consumer threads copy the
+                // WK*CC staged columns to C, 16 bytes per access where the
+                // row block lies inside C and C allows it.
+                const bool fast = p.c_vec && row0 + K::BM <= p.m;
+                const int64_t ldc = *s_ldc;
+#pragma unroll
+                for (int r0 = 0; r0 < K::KCW; r0 += K::CC) {
+                    named_bar_sync(1, K::NT);
+                    if (!aborted) {
+#pragma unroll
+                        for (int cc = 0; cc < K::CC; ++cc)
+#pragma unroll
+                            for (int v = 0; v < K::NV; ++v) {
+                                T tmp[K::V];
+#pragma unroll
+                                for (int e = 0; e < K::V; ++e) tmp[e] = acc[v * K::V + e][r0 + cc];
+                                *reinterpret_cast<vec_t *>(sRed + (wk * K::CC + cc) * K::BM + row_of(v)) =
+                                    K::VT::make(tmp);
+                            }
+                    }
+                    named_bar_sync(1, K::NT);
+                    if (!aborted) {
+                        if (fast) {
+#pragma unroll 2
+                            for (int q = 0; q < (K::WK * K::CC * K::BM) / (4 * K::NT); ++q) {
+                                const int e = 4 * (tid + q * K::NT);
+                                const int slot = e / K::BM;
+                                const int row = e - slot * K::BM;
+                                const int c = (slot / K::CC) * K::KCW + r0 + (slot % K::CC);
+                                if (c < p.k)
+                                    *reinterpret_cast<float4 *>(C + row0 + row + (int64_t)c * ldc) =
+                                        *reinterpret_cast<const float4 *>(sRed + e);
+                            }
+                        } else {
+#pragma unroll 4
+                            for (int q = 0; q < (K::WK * K::CC * K::BM) / K::NT; ++q) {
+                                const int e = tid + q * K::NT;
+                                const int slot = e / K::BM;
+                                const int row = e - slot * K::BM;
+                                const int c = (slot / K::CC) * K::KCW + r0 + (slot % K::CC);
+                                if (c < p.k && row0 + row < p.m) C[row0 + row + (int64_t)c * ldc] = sRed[e];
+                            }
+                        }
+                    }
+                }
+            } else if constexpr (K::WC == 1) {
                 if (whole) {
                     if (!aborted) {
                         // Fast path: the row block lies inside C, all its columns are
