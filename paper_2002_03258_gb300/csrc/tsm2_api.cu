@@ -168,6 +168,18 @@ tsm2_status encode_2d(CUtensorMap *map, int elem, const void *base, int64_t rows
     return TSM2_SUCCESS;
 }
 
+// ---- C-column widths --------------------------------------------------------
+
+// Smallest compiled C-column width (KC) that holds a chunk of k columns: the
+// kernels compute all KC columns (padding columns of B read as zero), so a
+// close fit saves FMAs in the FMA-bound shapes.
+int kc_for(int k) {
+    static const int widths[] = {2, 4, 8, 12, 16, 24, 32};
+    for (int w : widths)
+        if (w >= k) return w;
+    return 32;
+}
+
 // ---- argument checks ---------------------------------------------------------
 
 bool ranges_overlap(const void *a, size_t abytes, const void *b, size_t bbytes) {
@@ -252,8 +264,7 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
             if (e != cudaSuccess) return cuda_error(e, "simple kernel launch");
             continue;
         }
-        int kc = 2;
-        while (kc < g.k) kc *= 2;
+        int kc = kc_for(g.k);
         if (staged_l && kc < 4) kc = 4;  // staged-B TSM2L: C columns in groups of four
         const StreamShape *shape = stream_shape(elem, staged_l ? 't' : op, kc);
         if (op == 'l' && !staged_l) {
@@ -727,8 +738,7 @@ tsm2_status gemm_r32_noalloc(int64_t m, int64_t n, int64_t k, const float *A, in
             if (e != cudaSuccess) return cuda_error(e, "simple kernel launch");
             continue;
         }
-        int kc = 2;
-        while (kc < g.k) kc *= 2;
+        const int kc = kc_for(g.k);
         const StreamShape *shape = stream_shape(elem, 'r', kc);
         if (!shape) return set_error(TSM2_ERR_UNSUPPORTED, "%s: no kernel configuration for k chunk %d", fn, g.k);
         const int64_t num_rb = (m + shape->BM - 1) / shape->BM;
@@ -1187,8 +1197,7 @@ tsm2_status tsm2_batch_plan_create_s(int nprob, const tsm2_problem_s *probs, int
         const int kcmax = op == 'l' ? 32 : 16;
         for (int64_t c0 = 0; c0 < q.k; c0 += kcmax) {
             const int kk = (int)std::min<int64_t>(kcmax, q.k - c0);
-            int kc = 2;
-            while (kc < kk) kc *= 2;
+            int kc = kc_for(kk);
             if (op == 'r' && merge_r) kc = 16;
             if (op == 'l' && merge_l) kc = 32;
             const BatchClass *cls = batch_class(op == 'l' && wide ? 'w' : op, kc);

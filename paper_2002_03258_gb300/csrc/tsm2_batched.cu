@@ -384,12 +384,18 @@ BatchClass class_of(char op, const char *name) {
 }
 
 const BatchClass kClasses[] = {
-    class_of<R32<2>>('r', "br_f32_kc2"),  class_of<R32<4>>('r', "br_f32_kc4"),  class_of<R32<8>>('r', "br_f32_kc8"),
-    class_of<R32<16>>('r', "br_f32_kc16"), class_of<L32<2>>('l', "bl_f32_kc2"),  class_of<L32<4>>('l', "bl_f32_kc4"),
-    class_of<L32<8>>('l', "bl_f32_kc8"),  class_of<L32<16>>('l', "bl_f32_kc16"), class_of<L32<32>>('l', "bl_f32_kc32"),
-    class_of<W32N<2>>('w', "bw_f32_kc2"),  class_of<W32N<4>>('w', "bw_f32_kc4"),  class_of<W32N<8>>('w', "bw_f32_kc8"),
-    class_of<W32N<16>>('w', "bw_f32_kc16"), class_of<W32N<32>>('w', "bw_f32_kc32"),
+    class_of<R32<2>>('r', "br_f32_kc2"),    class_of<R32<4>>('r', "br_f32_kc4"),
+    class_of<R32<8>>('r', "br_f32_kc8"),    class_of<R32<12>>('r', "br_f32_kc12"),
+    class_of<R32<16>>('r', "br_f32_kc16"),  class_of<L32<2>>('l', "bl_f32_kc2"),
+    class_of<L32<4>>('l', "bl_f32_kc4"),    class_of<L32<8>>('l', "bl_f32_kc8"),
+    class_of<L32<12>>('l', "bl_f32_kc12"),  class_of<L32<16>>('l', "bl_f32_kc16"),
+    class_of<L32<24>>('l', "bl_f32_kc24"),  class_of<L32<32>>('l', "bl_f32_kc32"),
+    class_of<W32N<2>>('w', "bw_f32_kc2"),   class_of<W32N<4>>('w', "bw_f32_kc4"),
+    class_of<W32N<8>>('w', "bw_f32_kc8"),   class_of<W32N<12>>('w', "bw_f32_kc12"),
+    class_of<W32N<16>>('w', "bw_f32_kc16"), class_of<W32N<24>>('w', "bw_f32_kc24"),
+    class_of<W32N<32>>('w', "bw_f32_kc32"),
 };
+
 
 }  // namespace
 

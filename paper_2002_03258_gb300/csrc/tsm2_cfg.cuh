@@ -211,7 +211,7 @@ static_assert(4 * 32 * kProducerRegs + 8 * 32 * kConsumerRegs <= 384 * 168, "reg
 // TSM2R schedule: 1 x 8 warps split the inner columns of each stage.
 //   binary32: R = 8 rows per lane (two float4), BM = 256, BNS = 32.
 //   binary64: R = 4 rows per lane (two double2), BM = 128, BNS = 32.
-//   KC = 16 keeps B row-major in shared memory (half the operand duplication).
+//   KC >= 12 keeps B row-major in shared memory (fewer operand duplications).
 #ifndef TSM2_R16_NV
 #define TSM2_R16_NV 2
 #endif
@@ -223,7 +223,7 @@ static_assert(4 * 32 * kProducerRegs + 8 * 32 * kConsumerRegs <= 384 * 168, "reg
 #endif
 template <int KC>
 using R32 = Cfg<float, KC, (KC >= 16 ? TSM2_R16_NV : 2), 1, 8, 1, (KC >= 16 ? TSM2_R16_JW : 4),
-                (KC >= 16 ? TSM2_R16_STAGES : 5), false, 0, (KC >= 16), (KC >= 16 && TSM2_R16_NV == 3 ? 128 : 0)>;
+                (KC >= 16 ? TSM2_R16_STAGES : 5), false, 0, (KC >= 12), (KC >= 16 && TSM2_R16_NV == 3 ? 128 : 0)>;
 template <int KC> using R64 = Cfg<double, KC, 2, 1, 8, 1, 4, 5, false, 0>;
 // TSM2L: resident B row-major wherever a warp's C columns are whole groups of
 // four (the B load at block start transposes; no packed copy needed).
@@ -253,7 +253,10 @@ struct WShape {
     bool sepi;
 };
 constexpr WShape w32_shape(int kc) {
-    return kc >= 32 ? WShape{2, 2, 4, 8, 5, false} : kc >= 16 ? WShape{2, 8, 1, 4, 5, true} : WShape{2, 8, 1, 4, 5, false};
+    return kc >= 32   ? WShape{2, 2, 4, 8, 5, false}
+           : kc >= 24 ? WShape{2, 4, 2, 8, 5, false}   // 12 columns per lane
+           : kc >= 16 ? WShape{2, 8, 1, 4, 5, true}
+                      : WShape{2, 8, 1, 4, 5, false};
 }
 template <int KC>
 using W32 = Cfg<float, KC, w32_shape(KC).nv, w32_shape(KC).wr, 1, w32_shape(KC).wk, w32_shape(KC).jw,
@@ -275,7 +278,9 @@ using W32N = Cfg<float, KC, w32n_shape(KC).nv, w32n_shape(KC).wr, 1, w32n_shape(
 // shared memory), 8 inner columns per stage for KC = 32; C columns in groups
 // of at least four (narrower k pads to KC = 4).
 constexpr WShape t32_shape(int kc) {
-    return kc >= 32 ? WShape{2, 4, 2, 8, 5, true} : kc >= 16 ? WShape{2, 8, 1, 4, 4, true} : WShape{2, 8, 1, 8, 3, false};
+    return kc >= 24   ? WShape{2, 4, 2, 8, 5, true}
+           : kc >= 16 ? WShape{2, 8, 1, 4, 4, true}
+                      : WShape{2, 8, 1, 8, 3, false};
 }
 template <int KC>
 using T32 = Cfg<float, KC, t32_shape(KC).nv, t32_shape(KC).wr, 1, t32_shape(KC).wk, t32_shape(KC).jw, t32_shape(KC).st,

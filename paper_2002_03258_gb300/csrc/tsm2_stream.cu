@@ -517,23 +517,30 @@ struct Entry {
 #define TSM2_ENTRY(OP, CFG, NAME) Entry{OP, shape_of<CFG>(NAME), &launch_cfg<CFG>}
 
 const Entry kEntries[] = {
-    TSM2_ENTRY('r', R32<2>, "r_f32_kc2"),   TSM2_ENTRY('r', R32<4>, "r_f32_kc4"),
-    TSM2_ENTRY('r', R32<8>, "r_f32_kc8"),   TSM2_ENTRY('r', R32<16>, "r_f32_kc16"),
-    TSM2_ENTRY('r', R64<2>, "r_f64_kc2"),   TSM2_ENTRY('r', R64<4>, "r_f64_kc4"),
-    TSM2_ENTRY('r', R64<8>, "r_f64_kc8"),   TSM2_ENTRY('r', R64<16>, "r_f64_kc16"),
-    TSM2_ENTRY('l', L32<2>, "l_f32_kc2"),   TSM2_ENTRY('l', L32<4>, "l_f32_kc4"),
-    TSM2_ENTRY('l', L32<8>, "l_f32_kc8"),   TSM2_ENTRY('l', L32<16>, "l_f32_kc16"),
-    TSM2_ENTRY('l', L32<32>, "l_f32_kc32"), TSM2_ENTRY('l', L64<2>, "l_f64_kc2"),
-    TSM2_ENTRY('l', L64<4>, "l_f64_kc4"),   TSM2_ENTRY('l', L64<8>, "l_f64_kc8"),
-    TSM2_ENTRY('l', L64<16>, "l_f64_kc16"), TSM2_ENTRY('l', L64<32>, "l_f64_kc32"),
-    TSM2_ENTRY('w', W32<2>, "lw_f32_kc2"),  TSM2_ENTRY('w', W32<4>, "lw_f32_kc4"),
-    TSM2_ENTRY('w', W32<8>, "lw_f32_kc8"),  TSM2_ENTRY('w', W32<16>, "lw_f32_kc16"),
+    TSM2_ENTRY('r', R32<2>, "r_f32_kc2"),    TSM2_ENTRY('r', R32<4>, "r_f32_kc4"),
+    TSM2_ENTRY('r', R32<8>, "r_f32_kc8"),    TSM2_ENTRY('r', R32<12>, "r_f32_kc12"),
+    TSM2_ENTRY('r', R32<16>, "r_f32_kc16"),  TSM2_ENTRY('r', R64<2>, "r_f64_kc2"),
+    TSM2_ENTRY('r', R64<4>, "r_f64_kc4"),    TSM2_ENTRY('r', R64<8>, "r_f64_kc8"),
+    TSM2_ENTRY('r', R64<12>, "r_f64_kc12"),  TSM2_ENTRY('r', R64<16>, "r_f64_kc16"),
+    TSM2_ENTRY('l', L32<2>, "l_f32_kc2"),    TSM2_ENTRY('l', L32<4>, "l_f32_kc4"),
+    TSM2_ENTRY('l', L32<8>, "l_f32_kc8"),    TSM2_ENTRY('l', L32<12>, "l_f32_kc12"),
+    TSM2_ENTRY('l', L32<16>, "l_f32_kc16"),  TSM2_ENTRY('l', L32<24>, "l_f32_kc24"),
+    TSM2_ENTRY('l', L32<32>, "l_f32_kc32"),  TSM2_ENTRY('l', L64<2>, "l_f64_kc2"),
+    TSM2_ENTRY('l', L64<4>, "l_f64_kc4"),    TSM2_ENTRY('l', L64<8>, "l_f64_kc8"),
+    TSM2_ENTRY('l', L64<12>, "l_f64_kc12"),  TSM2_ENTRY('l', L64<16>, "l_f64_kc16"),
+    TSM2_ENTRY('l', L64<24>, "l_f64_kc24"),  TSM2_ENTRY('l', L64<32>, "l_f64_kc32"),
+    TSM2_ENTRY('w', W32<2>, "lw_f32_kc2"),   TSM2_ENTRY('w', W32<4>, "lw_f32_kc4"),
+    TSM2_ENTRY('w', W32<8>, "lw_f32_kc8"),   TSM2_ENTRY('w', W32<12>, "lw_f32_kc12"),
+    TSM2_ENTRY('w', W32<16>, "lw_f32_kc16"), TSM2_ENTRY('w', W32<24>, "lw_f32_kc24"),
     TSM2_ENTRY('w', W32<32>, "lw_f32_kc32"),
-    TSM2_ENTRY('t', T32<4>, "lt_f32_kc4"),  TSM2_ENTRY('t', T32<8>, "lt_f32_kc8"),
-    TSM2_ENTRY('t', T32<16>, "lt_f32_kc16"), TSM2_ENTRY('t', T32<32>, "lt_f32_kc32"),
-    TSM2_ENTRY('t', T64<4>, "lt_f64_kc4"),  TSM2_ENTRY('t', T64<8>, "lt_f64_kc8"),
-    TSM2_ENTRY('t', T64<16>, "lt_f64_kc16"), TSM2_ENTRY('t', T64<32>, "lt_f64_kc32"),
+    TSM2_ENTRY('t', T32<4>, "lt_f32_kc4"),   TSM2_ENTRY('t', T32<8>, "lt_f32_kc8"),
+    TSM2_ENTRY('t', T32<12>, "lt_f32_kc12"), TSM2_ENTRY('t', T32<16>, "lt_f32_kc16"),
+    TSM2_ENTRY('t', T32<24>, "lt_f32_kc24"), TSM2_ENTRY('t', T32<32>, "lt_f32_kc32"),
+    TSM2_ENTRY('t', T64<4>, "lt_f64_kc4"),   TSM2_ENTRY('t', T64<8>, "lt_f64_kc8"),
+    TSM2_ENTRY('t', T64<12>, "lt_f64_kc12"), TSM2_ENTRY('t', T64<16>, "lt_f64_kc16"),
+    TSM2_ENTRY('t', T64<24>, "lt_f64_kc24"), TSM2_ENTRY('t', T64<32>, "lt_f64_kc32"),
 };
+
 
 }  // namespace
 

@@ -49,10 +49,12 @@ def run(op, dtype, m, n, k, lda=None, ldb=None, ldc=None, offA=0, offB=0, offC=0
 R_SHAPES = [
     (1, 1, 1), (31, 33, 3), (257, 100, 2), (1000, 1023, 8), (1023, 1000, 16), (2049, 777, 5),
     (300, 5000, 4), (4097, 300, 17), (10241, 64, 7), (128, 4096, 16), (5000, 31, 33),
+    (3001, 2000, 12), (1000, 777, 10), (2500, 1500, 28),
 ]
 L_SHAPES = [
     (100003, 8, 8), (65537, 16, 16), (33333, 32, 32), (1000, 3, 5), (5000, 64, 64), (777, 33, 40),
     (1, 1, 1), (4096, 24, 2), (70001, 17, 9),
+    (500001, 24, 24), (300000, 20, 20), (30000, 12, 12), (40000, 11, 9), (2000001, 12, 12),
 ]
 
 

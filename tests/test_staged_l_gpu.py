@@ -25,7 +25,7 @@ def _defaults():
 
 STAGED_SHAPES = [
     (5000, 65, 8), (100003, 100, 16), (30001, 300, 32), (2049, 1000, 3), (70001, 129, 33), (10, 200, 64),
-    (4096, 96, 1), (50000, 80, 100), (1, 65, 2),
+    (4096, 96, 1), (50000, 80, 100), (1, 65, 2), (30001, 300, 24), (5000, 100, 12),
 ]
 
 
