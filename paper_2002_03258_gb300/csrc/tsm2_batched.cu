@@ -158,12 +158,7 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
                 // Resident B of this problem; every warp finished the previous
                 // problem's last piece (its epilogue) before reaching here.
                 named_bar_sync(1, K::NT);
-                const T *Bp = static_cast<const T *>(pd->B);
-                for (int t = tid; t < K::KC * K::NRES; t += K::NT) {
-                    const int j = K::BT ? t / K::KC : t % K::NRES;
-                    const int c = K::BT ? t % K::KC : t / K::NRES;
-                    sBres[t] = (j < pd->n && c < pd->k) ? Bp[j + (int64_t)c * pd->ldb] : T(0);
-                }
+                load_resident_b<K>(sBres, static_cast<const T *>(pd->B), pd->n, pd->k, pd->ldb, tid, K::NT);
                 named_bar_sync(1, K::NT);
             }
         }
@@ -189,7 +184,7 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
                 const T *b_st;
                 int bstride;
                 if constexpr (K::BRES) {
-                    b_st = K::BT ? sBres + (size_t)jc * K::BNS * K::KC : sBres + jc * K::BNS;
+                    b_st = resident_b_stage<K>(sBres, jc);
                     bstride = K::NRES;
                 } else {
                     b_st = sB + (size_t)s * K::B_STAGE;
@@ -219,7 +214,11 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
                 const int64_t rbg = pd->rb_begin + rb64;  // global row block: counters and slots
                 T *ws = p.ws;
                 if constexpr (K::WC == 1) {
-                    if (whole && !aborted) {
+                    // Not conditional on `aborted`: after a timeout C is
+                    // undefined anyway (the host reports the error), both
+                    // branches stay inside C, and the guard makes ptxas spill
+                    // wide accumulator tiles.
+                    if (whole) {
                         T *cw = C + row0 + (int64_t)kbase * ldc;
                         const bool fast = pd->c_vec && row0 + K::BM <= m && kbase + K::KCW <= kk;
 #pragma unroll

@@ -194,6 +194,26 @@ __device__ __forceinline__ void consume_stage(const typename K::T *a_st, const t
     }
 }
 
+// Resident B (n <= NRES inner indices, KC columns) into shared memory, zero
+// beyond n and k so padded lanes contribute exact zeros: column c at
+// sBres[c*NRES + j], or row-major (K::BT) (j, c) at sBres[j*KC + c].
+template <class K>
+__device__ __forceinline__ void load_resident_b(typename K::T *sBres, const typename K::T *B, int64_t n, int k,
+                                                int64_t ldb, int tid, int nthreads) {
+    using T = typename K::T;
+    for (int t = tid; t < K::KC * K::NRES; t += nthreads) {
+        const int j = K::BT ? t / K::KC : t % K::NRES;
+        const int c = K::BT ? t % K::KC : t / K::NRES;
+        sBres[t] = (j < n && c < k) ? B[j + (int64_t)c * ldb] : T(0);
+    }
+}
+
+// The part of resident B that pairs with stage jc (inner indices jc*BNS ..).
+template <class K>
+__device__ __forceinline__ const typename K::T *resident_b_stage(const typename K::T *sBres, int jc) {
+    return K::BT ? sBres + (size_t)jc * K::BNS * K::KC : sBres + jc * K::BNS;
+}
+
 // Block index that owns group x under the partition gs(g) = floor(g*NG/G).
 __device__ __forceinline__ int64_t owner_of(int64_t x, int64_t G, int64_t NG) {
     return ((x + 1) * G + NG - 1) / NG - 1;
@@ -240,20 +260,21 @@ using L32 = Cfg<float, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, 5, t
 template <int KC> using L64 = Cfg<double, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, 5, true, 64>;
 // TSM2L schedule for tall A (binary32): R = 8 rows per lane, so every B value
 // read from shared memory (one wavefront per broadcast value) feeds twice the
-// FMAs; the C columns are split over WK = 1, 2, 4 warps (KC <= 8, 16, 32) so a
-// lane never holds more than 64 accumulators.  Chosen when there are enough
-// row blocks for an even spread over the SMs.
-// KC = 16 keeps 16 C columns per lane (128 accumulators, WK = 1), so each A
-// value read from shared memory feeds 16 columns instead of 8; C then goes
-// out through shared memory (SEPI).  For KC = 32 the same width (WK = 2)
-// measured slower with resident B: its row blocks are 4 stages long and the
-// staged C copy stalls the warps that compute; 8 columns per lane stay.
+// FMAs; the C columns are split over WK = 1 or 2 warps.  Chosen when there are
+// enough row blocks for an even spread over the SMs.
+// KC = 32: 16 C columns per lane (128 accumulators, WK = 2, 1024-row blocks),
+// stored straight from registers.  n = k = 32 is FMA-bound on chip (32 FMAs
+// per 8 bytes of A and C), and against 8 columns per lane this halves the
+// shared-memory reads of A per FMA: 75% -> 92% of HBM at 2^23 rows.
+// KC = 16 keeps 16 C columns per lane (128 accumulators, WK = 1) and writes C
+// through shared memory (SEPI), measured faster than storing from registers
+// for this shape.
 struct WShape {
     int nv, wr, wk, jw, st;
     bool sepi;
 };
 constexpr WShape w32_shape(int kc) {
-    return kc >= 32   ? WShape{2, 2, 4, 8, 5, false}
+    return kc >= 32   ? WShape{2, 4, 2, 8, 5, false}   // 16 columns per lane
            : kc >= 24 ? WShape{2, 4, 2, 8, 5, false}   // 12 columns per lane
            : kc >= 16 ? WShape{2, 8, 1, 4, 5, true}
                       : WShape{2, 8, 1, 4, 5, false};

@@ -107,17 +107,6 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
         *s_ldc = p.ldc;
         fence_mbar_init();
     }
-    if constexpr (K::BRES) {
-        // Whole of B (n <= NRES) once per block, column c at sBres[c*NRES + j]
-        // (row-major configurations: sBres[j*KC + c]), zero beyond n and k so
-        // padded lanes contribute exact zeros.
-        const T *B = static_cast<const T *>(p.B);
-        for (int t = threadIdx.x; t < K::KC * K::NRES; t += K::THREADS) {
-            const int j = K::BT ? t / K::KC : t % K::NRES;
-            const int c = K::BT ? t % K::KC : t / K::NRES;
-            sBres[t] = (j < p.n && c < p.k) ? B[j + (int64_t)c * p.ldb] : T(0);
-        }
-    }
     __syncthreads();
 
     if (warp < 4) {
@@ -166,6 +155,12 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 
     // ---------------- consumers ----------------
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
+    if constexpr (K::BRES) {
+        // Whole of B (n <= NRES) once per block, loaded by the consumers
+        // while the producer's first copies of A are already in flight.
+        load_resident_b<K>(sBres, static_cast<const T *>(p.B), p.n, p.k, p.ldb, threadIdx.x - 128, K::NT);
+        named_bar_sync(1, K::NT);
+    }
     const int cwarp = warp - 4;                 // consumer warp 0 .. NW-1
     const int wk = cwarp % K::WK;               // group of C columns
     const int wc = (cwarp / K::WK) % K::WC;     // inner-column group
@@ -212,7 +207,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             const T *b_st;
             int bstride;
             if constexpr (K::BRES) {
-                b_st = K::BT ? sBres + (size_t)jc * K::BNS * K::KC : sBres + jc * K::BNS;
+                b_st = resident_b_stage<K>(sBres, jc);
                 bstride = K::NRES;
             } else {
                 b_st = sB + (size_t)s * K::B_STAGE;
@@ -295,7 +290,11 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                 }
             } else if constexpr (K::WC == 1) {
                 if (whole) {
-                    if (!aborted) {
+                    // Not conditional on `aborted`: after a timeout C is undefined
+                    // anyway (the host reports the error), both branches stay
+                    // inside C, and a guard here makes ptxas spill the 128
+                    // accumulators of the wide TSM2L shapes.
+                    {
                         // Fast path: the row block lies inside C, all its columns are
                         // live and C allows 16-byte stores: unpredicated vector stores.
                         const bool fast = p.c_vec && row0 + K::BM <= p.m && kbase + K::KCW <= p.k;

@@ -49,6 +49,9 @@ def device_matrix(rows, cols, dtype, seed, mid, dist="uniform"):
     ("l", np.float32, 3_000_000, 16, 16, "uniform"),
     ("l", np.float32, 3_000_000, 20, 20, "int_small"),
     ("l", np.float32, 3_000_000, 32, 32, "uniform"),
+    # 16 C columns per lane (k chunk 25..32): ragged rows, inner dimension
+    # and columns, so the second column warp stores through the predicated path
+    ("l", np.float32, 1_000_004, 30, 29, "uniform"),
 ])
 def test_fullsize_sampled_rows(op, dtype, m, n, k, dist):
     import paper_2002_03258_gb300 as pkg
@@ -63,7 +66,7 @@ def test_fullsize_sampled_rows(op, dtype, m, n, k, dist):
     assert pkg.tsm2_get_device_status(0) == 0
     cfg = pkg.tsm2_last_config()
     assert not cfg.startswith("simple")
-    if op == "l" and dtype == np.float32 and m >= 3_000_000:
+    if op == "l" and dtype == np.float32 and m in (3_000_000, 1_000_004):
         assert cfg.startswith("lw_"), cfg
     rows = sample_rows(m)
     got = C[torch.from_numpy(rows).cuda()].cpu().numpy()

@@ -55,6 +55,7 @@ L_SHAPES = [
     (100003, 8, 8), (65537, 16, 16), (33333, 32, 32), (1000, 3, 5), (5000, 64, 64), (777, 33, 40),
     (1, 1, 1), (4096, 24, 2), (70001, 17, 9),
     (500001, 24, 24), (300000, 20, 20), (30000, 12, 12), (40000, 11, 9), (2000001, 12, 12),
+    (1000005, 32, 29),
 ]
 
 
