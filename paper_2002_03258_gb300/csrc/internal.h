@@ -100,7 +100,7 @@ cudaError_t rankk_launch(int elem, int64_t m, int64_t n, int k, const void *dC, 
 struct BF16Launch {
     int64_t m, n;
     int k;               // <= 16
-    CUtensorMap mapHi;   // A_hi: bf16 dims {m, n}, box {64, 64}, 128-byte swizzle
+    CUtensorMap mapHi;   // A_hi: bf16 dims {m, n}, box {64, bf16_bk(hilo)}, 128-byte swizzle
     CUtensorMap mapLo;   // A_lo (when hilo)
     bool hilo;
     const void *bpieces; // prepared B pieces (bf16_prep_b)
@@ -113,9 +113,9 @@ struct BF16Launch {
     int grid;
 };
 int bf16_bm();
-int bf16_bk();
-size_t bf16_bpieces_bytes(int64_t n);
-cudaError_t bf16_prep_b(int64_t n, int k, const float *B, int64_t ldb, void *out, cudaStream_t stream);
+int bf16_bk(bool hilo);  // inner columns per pipeline stage
+size_t bf16_bpieces_bytes(int64_t n, bool hilo);
+cudaError_t bf16_prep_b(int64_t n, int k, const float *B, int64_t ldb, void *out, bool hilo, cudaStream_t stream);
 cudaError_t bf16_launch(const BF16Launch &L, cudaStream_t stream);
 cudaError_t bf16_simple_launch(int64_t m, int64_t n, int k, const void *A_hi, const void *A_lo, int64_t lda,
                                const float *B, int64_t ldb, float *C, int64_t ldc, cudaStream_t stream);

@@ -511,29 +511,29 @@ tsm2_status gemm_bf16(int64_t m, int64_t n, int64_t k, const void *A_hi, const v
         L.n = n;
         L.k = kk;
         L.hilo = A_lo != nullptr;
-        st = encode_2d_ex(&L.mapHi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A_hi, m, n, lda, 64, bf16_bk(),
+        st = encode_2d_ex(&L.mapHi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A_hi, m, n, lda, 64, bf16_bk(L.hilo),
                           CU_TENSOR_MAP_SWIZZLE_128B);
         if (st != TSM2_SUCCESS) return st;
         if (L.hilo) {
-            st = encode_2d_ex(&L.mapLo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A_lo, m, n, lda, 64, bf16_bk(),
+            st = encode_2d_ex(&L.mapLo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A_lo, m, n, lda, 64, bf16_bk(L.hilo),
                               CU_TENSOR_MAP_SWIZZLE_128B);
             if (st != TSM2_SUCCESS) return st;
         }
         const int64_t num_rb = (m + bf16_bm() - 1) / bf16_bm();
-        const int64_t upr = (n + bf16_bk() - 1) / bf16_bk();
+        const int64_t upr = (n + bf16_bk(L.hilo) - 1) / bf16_bk(L.hilo);
         const int64_t ngroups = num_rb * upr;
         int64_t grid = dev->sm_count;
         if (ngroups / 4 < grid) grid = ngroups / 4;
         if (g_grid_override > 0) grid = g_grid_override;
         if (grid > ngroups) grid = ngroups;
         if (grid < 1) grid = 1;
-        const size_t pieces = (bf16_bpieces_bytes(n) + 255) / 256 * 256;
+        const size_t pieces = (bf16_bpieces_bytes(n, L.hilo) + 255) / 256 * 256;
         const size_t slots = (size_t)(grid + num_rb) * 16 * bf16_bm() * 4;
         void *ws = nullptr;
         int *counters = nullptr;
         st = workspace(stream, (size_t)num_rb * sizeof(int), pieces + slots, &ws, &counters);
         if (st != TSM2_SUCCESS) return st;
-        e = bf16_prep_b(n, kk, Bc, ldb, ws, stream);
+        e = bf16_prep_b(n, kk, Bc, ldb, ws, L.hilo, stream);
         if (e != cudaSuccess) return cuda_error(e, "bf16 B split kernel launch");
         L.bpieces = ws;
         L.ws = static_cast<char *>(ws) + pieces;

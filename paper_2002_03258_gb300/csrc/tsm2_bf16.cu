@@ -10,10 +10,14 @@
 //    (each piece the round-to-nearest-even of the remainder), by a small prep
 //    kernel that also lays them out pre-tiled in the canonical K-major
 //    no-swizzle layout of the MMA B operand (8 x 16-byte core matrices).
-//  * A tiles (512 rows x 32 inner columns per stage, eight 64-row boxes, so
+//  * A tiles (512 rows x BK inner columns per stage, eight 64-row boxes, so
 //    DRAM sees 1 KB runs per column) arrive by TMA with the 128-byte swizzle,
 //    i.e. in the canonical MN-major SW128 layout of the MMA A operand (A is
 //    column-major, rows contiguous); each stage is four M = 128 row tiles.
+//    BK = 64 for plain A (a 64 KB tile per stage) and 32 for hi+lo (two 32 KB
+//    tiles): every stage hand-off (full/empty barriers, copy issue, MMA
+//    commit) costs a fixed time, which 32 KB stages could not hide (79% of
+//    HBM for plain A against 90% with 64 KB stages).
 //  * One thread issues tcgen05.mma.kind::f16 (M = 128, N = 16, K = 16,
 //    bf16 x bf16 -> f32) into a TMEM accumulator:
 //        plain:  C += A * B1 + A * B2              (B to 16 bits: below the
@@ -47,21 +51,33 @@ constexpr int kMM = 128;          // MMA M = TMEM lanes
 constexpr int kSub = 4;           // MMA row tiles per unit
 constexpr int kBM = kSub * kMM;   // 512 rows per unit: 1 KB contiguous per column of A
 constexpr int kKC = 16;           // C columns = MMA N
-constexpr int kBK = 32;           // inner columns per stage
-constexpr int kKSteps = kBK / 16; // MMA K steps per stage
-constexpr int kMaxStages = 8;     // stages are sized at run time: 6 (plain) or 3 (hi+lo)
+constexpr int kMaxStages = 8;     // stages are sized at run time: 3 (plain and hi+lo)
 constexpr int kPieces = 3;        // bfloat16 pieces of B
-constexpr int kBox = 64 * kBK * 2;                     // one 64-row TMA box: 4 KB
-constexpr int kATile = kBM * kBK * 2;                  // 32 KB per A tile (8 boxes)
-constexpr int kBBlock = kPieces * kKSteps * 512;       // 3 KB of B pieces per stage
-constexpr int kStageHiLo = 2 * kATile + kBBlock;       // 67 KB
-constexpr int kStagePlain = kATile + kBBlock;          // 35 KB
+// Per-stage geometry for BK inner columns per stage.
+template <int BK_>
+struct Depth {
+    static constexpr int BK = BK_;
+    static constexpr int KSteps = BK / 16;                   // MMA K steps per stage
+    static constexpr int Box = 64 * BK * 2;                  // one 64-row TMA box
+    static constexpr int ATile = kBM * BK * 2;               // one A tile (8 boxes)
+    static constexpr int BBlock = kPieces * KSteps * 512;    // B pieces per stage
+};
+constexpr int kBKPlain = 64;
+constexpr int kBKHiLo = 32;
+using DPlain = Depth<kBKPlain>;
+using DHiLo = Depth<kBKHiLo>;
+constexpr int kStagePlain = DPlain::ATile + DPlain::BBlock;    // 70 KB
+constexpr int kStageHiLo = 2 * DHiLo::ATile + DHiLo::BBlock;   // 67 KB
 constexpr int kNBuf = 4;                               // TMEM accumulator buffers
 constexpr int kBufCols = kSub * kKC;                   // 64 columns per buffer
 constexpr int kTmemCols = kNBuf * kBufCols;            // 256 columns
 constexpr int kSmemBudget = 210 * 1024;                // ring bytes (barriers follow)
-static_assert(kSmemBudget / kStageHiLo >= 3 && kSmemBudget + 1024 + 512 <= 227 * 1024, "shared memory budget");
-static_assert(kStageHiLo % 1024 == 0 && kStagePlain % 1024 == 0 && kBox % 1024 == 0, "1 KB alignment of A boxes");
+static_assert(kSmemBudget / kStageHiLo >= 3 && kSmemBudget / kStagePlain >= 3 &&
+                  kSmemBudget + 1024 + 512 <= 227 * 1024,
+              "shared memory budget");
+static_assert(kStageHiLo % 1024 == 0 && kStagePlain % 1024 == 0 && DPlain::Box % 1024 == 0 &&
+                  DHiLo::Box % 1024 == 0,
+              "1 KB alignment of A boxes");
 
 // Instruction descriptor, kind::f16: D f32, A bf16, B bf16, A MN-major
 // (column-major A: rows contiguous), B K-major, N = 16, M = 128.
@@ -142,8 +158,10 @@ struct BParams {
 
 __device__ __forceinline__ int64_t owner_b(int64_t x, int64_t G, int64_t NG) { return ((x + 1) * G + NG - 1) / NG - 1; }
 
+template <int BK>
 __global__ void __launch_bounds__(192, 1)
 bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ CUtensorMap mapLo, const BParams p) {
+    using D = Depth<BK>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = smem_aligned<1024>(smem_raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kSmemBudget);
@@ -196,7 +214,7 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
             prefetch_tensormap(&mapHi);
             if (p.hilo) prefetch_tensormap(&mapLo);
             const uint64_t policy = l2_policy_evict_first();
-            const uint32_t tx = (uint32_t)((p.hilo ? 2 : 1) * kATile + kBBlock);
+            const uint32_t tx = (uint32_t)((p.hilo ? 2 : 1) * D::ATile + D::BBlock);
             int s = 0;
             uint32_t ph = 0, issued = 0, last_par = 0;
             int rb = (int)(u_begin / p.upr);
@@ -210,13 +228,14 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
                 }
                 unsigned char *st = smem + s * sbytes;
                 mbar_arrive_expect_tx(&full[s], tx);
-                const int32_t x0 = rb * kBM, y0 = kc * kBK;
+                const int32_t x0 = rb * kBM, y0 = kc * BK;
 #pragma unroll
                 for (int q = 0; q < kBM / 64; ++q) {
-                    tma_load_2d_hint(st + q * kBox, &mapHi, x0 + q * 64, y0, &full[s], policy);
-                    if (p.hilo) tma_load_2d_hint(st + kATile + q * kBox, &mapLo, x0 + q * 64, y0, &full[s], policy);
+                    tma_load_2d_hint(st + q * D::Box, &mapHi, x0 + q * 64, y0, &full[s], policy);
+                    if (p.hilo)
+                        tma_load_2d_hint(st + D::ATile + q * D::Box, &mapLo, x0 + q * 64, y0, &full[s], policy);
                 }
-                bulk_g2s(st + sbytes - kBBlock, p.bpieces + (size_t)kc * kBBlock, kBBlock, &full[s]);
+                bulk_g2s(st + sbytes - D::BBlock, p.bpieces + (size_t)kc * D::BBlock, D::BBlock, &full[s]);
                 issued |= 1u << s;
                 last_par = (last_par & ~(1u << s)) | (ph << s);
                 if (++s == nst) { s = 0; ph ^= 1u; }
@@ -257,20 +276,20 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
                 tc_fence_after();
                 const uint32_t st = smem_u32(smem + s * sbytes);
 #pragma unroll
-                for (int ks = 0; ks < kKSteps; ++ks) {
+                for (int ks = 0; ks < D::KSteps; ++ks) {
                     // B pieces: K-major, no swizzle: K-halves 128 B apart (LBO),
                     // 8-column groups of C 256 B apart (SBO).
-                    const uint32_t bb = st + sbytes - kBBlock + ks * 512;
+                    const uint32_t bb = st + sbytes - D::BBlock + ks * 512;
                     const uint64_t b1 = sdesc(bb, 128, 256, 0);
-                    const uint64_t b2 = sdesc(bb + kKSteps * 512, 128, 256, 0);
-                    const uint64_t b3 = sdesc(bb + 2 * kKSteps * 512, 128, 256, 0);
+                    const uint64_t b2 = sdesc(bb + D::KSteps * 512, 128, 256, 0);
+                    const uint64_t b3 = sdesc(bb + 2 * D::KSteps * 512, 128, 256, 0);
 #pragma unroll
                     for (int sub = 0; sub < kSub; ++sub) {
                         // A row tile sub: MN-major SW128, its two 64-row boxes
-                        // 4 KB apart (LBO), 8-column groups 1 KB apart (SBO).
-                        const uint32_t aoff = sub * 2 * kBox + ks * 2048;
-                        const uint64_t ahi = sdesc(st + aoff, kBox, 1024, 2);
-                        const uint64_t alo = sdesc(st + kATile + aoff, kBox, 1024, 2);
+                        // one box apart (LBO), 8-column groups 1 KB apart (SBO).
+                        const uint32_t aoff = sub * 2 * D::Box + ks * 2048;
+                        const uint64_t ahi = sdesc(st + aoff, D::Box, 1024, 2);
+                        const uint64_t alo = sdesc(st + D::ATile + aoff, D::Box, 1024, 2);
                         const uint32_t d = tmem + (uint32_t)(buf * kBufCols + sub * kKC);
                         umma_f16(d, ahi, b1, (gstart && ks == 0) ? 0u : 1u);
                         umma_f16(d, ahi, b2, 1u);
@@ -435,20 +454,22 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
 }
 
 // Split binary32 B (n x k, k <= 16) into three bfloat16 pieces, written in the
-// MMA B-operand layout [n/64 blocks][piece][kstep][core nb][core kb][8][8].
+// MMA B-operand layout [n/bk blocks][piece][kstep][core nb][core kb][8][8]
+// (bk inner columns per block, one block per pipeline stage).
 __global__ void bsplit_kernel(int64_t n, int k, const float *__restrict__ B, int64_t ldb, __nv_bfloat16 *out,
-                              int64_t nblocks) {
-    const int64_t total = nblocks * kPieces * kKSteps * 256;  // bf16 elements
+                              int64_t nblocks, int bk) {
+    const int ksteps = bk / 16;
+    const int64_t total = nblocks * kPieces * ksteps * 256;  // bf16 elements
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         int64_t q = t;
         const int e = (int)(q % 8); q /= 8;
         const int rr = (int)(q % 8); q /= 8;
         const int kb = (int)(q % 2); q /= 2;
         const int nb = (int)(q % 2); q /= 2;
-        const int ks = (int)(q % kKSteps); q /= kKSteps;
+        const int ks = (int)(q % ksteps); q /= ksteps;
         const int piece = (int)(q % kPieces); q /= kPieces;
         const int64_t blk = q;
-        const int64_t j = blk * kBK + ks * 16 + kb * 8 + e;
+        const int64_t j = blk * bk + ks * 16 + kb * 8 + e;
         const int c = nb * 8 + rr;
         const float b = (j < n && c < k) ? B[j + (int64_t)c * ldb] : 0.f;
         const __nv_bfloat16 b1 = __float2bfloat16_rn(b);
@@ -509,33 +530,42 @@ __global__ void split_kernel(int64_t rows, int64_t cols, const float *X, int64_t
 }  // namespace
 
 int bf16_bm() { return kBM; }
-int bf16_bk() { return kBK; }
-size_t bf16_bpieces_bytes(int64_t n) { return (size_t)((n + kBK - 1) / kBK) * kBBlock; }
+int bf16_bk(bool hilo) { return hilo ? kBKHiLo : kBKPlain; }
+size_t bf16_bpieces_bytes(int64_t n, bool hilo) {
+    const int bk = bf16_bk(hilo);
+    return (size_t)((n + bk - 1) / bk) * (hilo ? DHiLo::BBlock : DPlain::BBlock);
+}
 
-cudaError_t bf16_prep_b(int64_t n, int k, const float *B, int64_t ldb, void *out, cudaStream_t stream) {
-    const int64_t nblocks = (n + kBK - 1) / kBK;
-    const int64_t total = nblocks * kPieces * kKSteps * 256;
+cudaError_t bf16_prep_b(int64_t n, int k, const float *B, int64_t ldb, void *out, bool hilo, cudaStream_t stream) {
+    const int bk = bf16_bk(hilo);
+    const int64_t nblocks = (n + bk - 1) / bk;
+    const int64_t total = nblocks * kPieces * (bk / 16) * 256;
     int64_t grid = (total + 255) / 256;
     if (grid > 4096) grid = 4096;
-    bsplit_kernel<<<(unsigned)grid, 256, 0, stream>>>(n, k, B, ldb, static_cast<__nv_bfloat16 *>(out), nblocks);
+    bsplit_kernel<<<(unsigned)grid, 256, 0, stream>>>(n, k, B, ldb, static_cast<__nv_bfloat16 *>(out), nblocks, bk);
     return cudaGetLastError();
 }
 
-cudaError_t bf16_launch(const BF16Launch &L, cudaStream_t stream) {
+template <int BK>
+cudaError_t bf16_set_smem(int smem) {
     static std::mutex mu;
-    static uint64_t attr_done = 0;
-    const int smem = kSmemBudget + 1024 + 512;  // ring + 1 KB alignment slack + barriers
+    static uint64_t attr_done = 0;  // one bit per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        if (dev < 64 && !(attr_done & (1ull << dev))) {
-            e = cudaFuncSetAttribute(bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return e;
-            attr_done |= 1ull << dev;
-        }
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 64 && !(attr_done & (1ull << dev))) {
+        e = cudaFuncSetAttribute(bf16_kernel<BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_done |= 1ull << dev;
     }
+    return cudaSuccess;
+}
+
+cudaError_t bf16_launch(const BF16Launch &L, cudaStream_t stream) {
+    const int smem = kSmemBudget + 1024 + 512;  // ring + 1 KB alignment slack + barriers
+    cudaError_t e = L.hilo ? bf16_set_smem<kBKHiLo>(smem) : bf16_set_smem<kBKPlain>(smem);
+    if (e != cudaSuccess) return e;
     BParams p;
     p.m = L.m;
     p.n = L.n;
@@ -547,17 +577,21 @@ cudaError_t bf16_launch(const BF16Launch &L, cudaStream_t stream) {
     p.counters = L.counters;
     p.status = L.status;
     p.wait_ns = L.wait_ns;
-    p.upr = (L.n + kBK - 1) / kBK;
+    const int bk = bf16_bk(L.hilo);
+    p.upr = (L.n + bk - 1) / bk;
     p.ngroups = ((L.m + kBM - 1) / kBM) * p.upr;
     p.hilo = L.hilo ? 1 : 0;
-    // Plain: the tensor cores sum 8 stages (512 products per output) before
-    // each drain, far inside the bfloat16 representation error of A; hi+lo:
-    // one stage per drain, for binary32-like accuracy.
-    p.group = L.hilo ? 1 : 8;
+    // Plain: the tensor cores sum 4 stages (256 inner indices, 512 products
+    // per output) before each drain, far inside the bfloat16 representation
+    // error of A; hi+lo: one stage per drain, for binary32-like accuracy.
+    p.group = L.hilo ? 1 : 4;
     p.stage_bytes = L.hilo ? kStageHiLo : kStagePlain;
     p.stages = kSmemBudget / p.stage_bytes;
     if (p.stages > kMaxStages) p.stages = kMaxStages;
-    bf16_kernel<<<L.grid, 192, smem, stream>>>(L.mapHi, L.mapLo, p);
+    if (L.hilo)
+        bf16_kernel<kBKHiLo><<<L.grid, 192, smem, stream>>>(L.mapHi, L.mapLo, p);
+    else
+        bf16_kernel<kBKPlain><<<L.grid, 192, smem, stream>>>(L.mapHi, L.mapLo, p);
     return cudaGetLastError();
 }
 
