@@ -96,10 +96,11 @@ def test_tensor_core_integers_bit_exact(hilo):
     check(C, Aeff, B, hilo, exact=True)
 
 
+@pytest.mark.parametrize("hilo", [False, True])
 @pytest.mark.parametrize("grid", [1, 3, 50])
-def test_tensor_core_any_grid(grid):
-    C, Aeff, B, cfg = run(1500, 2500, 12, True, grid=grid)
-    check(C, Aeff, B, True)
+def test_tensor_core_any_grid(grid, hilo):
+    C, Aeff, B, cfg = run(1500, 2500, 12, hilo, grid=grid)
+    check(C, Aeff, B, hilo)
 
 
 def test_elementwise_path_unaligned_lda():
