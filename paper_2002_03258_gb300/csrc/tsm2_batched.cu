@@ -221,22 +221,30 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
                     if (whole) {
                         T *cw = C + row0 + (int64_t)kbase * ldc;
                         const bool fast = pd->c_vec && row0 + K::BM <= m && kbase + K::KCW <= kk;
+                        if (fast) {
 #pragma unroll
-                        for (int c = 0; c < K::KCW; ++c) {
+                            for (int c = 0; c < K::KCW; ++c) {
 #pragma unroll
-                            for (int v = 0; v < K::NV; ++v) {
-                                if (fast) {
+                                for (int v = 0; v < K::NV; ++v) {
                                     T tmp[K::V];
 #pragma unroll
                                     for (int e = 0; e < K::V; ++e) tmp[e] = acc[v * K::V + e][c];
                                     *reinterpret_cast<vec_t *>(cw + row_of(v)) = K::VT::make(tmp);
-                                } else if (kbase + c < kk) {
-#pragma unroll
-                                    for (int e = 0; e < K::V; ++e)
-                                        if (row0 + row_of(v) + e < m) cw[row_of(v) + e] = acc[v * K::V + e][c];
                                 }
+                                cw += ldc;
                             }
-                            cw += ldc;
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < K::KCW; ++c) {
+                                if (kbase + c < kk) {
+#pragma unroll
+                                    for (int v = 0; v < K::NV; ++v)
+#pragma unroll
+                                        for (int e = 0; e < K::V; ++e)
+                                            if (row0 + row_of(v) + e < m) cw[row_of(v) + e] = acc[v * K::V + e][c];
+                                }
+                                cw += ldc;
+                            }
                         }
                     }
                 } else {

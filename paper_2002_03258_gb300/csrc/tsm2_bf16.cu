@@ -18,22 +18,25 @@
 //    tiles): every stage hand-off (full/empty barriers, copy issue, MMA
 //    commit) costs a fixed time, which 32 KB stages could not hide (79% of
 //    HBM for plain A against 90% with 64 KB stages).
-//  * One thread issues tcgen05.mma.kind::f16 (M = 128, N = 16, K = 16,
-//    bf16 x bf16 -> f32) into a TMEM accumulator:
-//        plain:  C += A * B1 + A * B2              (B to 16 bits: below the
-//                                                   2^-9 representation error of A)
-//        hi+lo:  C += Ahi*(B1+B2+B3) + Alo*(B1+B2) (drops only Alo*B3,
-//                                                   < 2^-26 |A||B| per product)
+//  * One thread issues tcgen05.mma.kind::f16 (M = 128, K = 16, bf16 x bf16
+//    -> f32) into TMEM, one MMA per A operand with the B pieces side by side
+//    in N, each piece into its own 16 accumulator columns:
+//        plain:  [D1 D2]    += A   * [B1 B2]     (N = 32; B to 16 bits: below
+//                                                 the 2^-9 representation error of A)
+//        hi+lo:  [D1 D2 D3] += Ahi * [B1 B2 B3]  (N = 48)
+//                [D1 D2 D3] += Alo * [B1 B2 B3]
+//    so each A tile is read from shared memory once per K step, not once per
+//    piece (with N = 16 per piece the MMAs' A reads limited the kernel).
 //    tcgen05.commit releases each shared-memory stage back to the producer.
-//  * A group of stages accumulates into one of four TMEM buffers (4 x 64
-//    columns: 16 per row tile, so the MMAs can run groups ahead of the
-//    drain); four epilogue warps drain it with tcgen05.ld after every group
-//    (one TMEM lane = one row of C, the four row tiles' loads in flight
-//    together) and carry the sum over groups in registers with
-//    round-to-nearest binary32 adds.  hi+lo drains after every stage (the
-//    tensor cores' own accumulation then covers 20 products' worth of
-//    partial sums only, which keeps hi+lo at binary32-like accuracy); plain
-//    drains every 8 stages, far below its bfloat16 representation error.
+//  * A group of stages accumulates into one of the TMEM buffers (4 for plain,
+//    2 for hi+lo, so the MMAs can run groups ahead of the drain); four
+//    epilogue warps drain it with tcgen05.ld after every group (one TMEM lane
+//    = one row of C), add the pieces smallest first and carry the sum over
+//    groups in registers with round-to-nearest binary32 adds.  hi+lo drains
+//    after every stage (the tensor cores' own accumulation then covers one
+//    stage's products only, which keeps hi+lo at binary32-like accuracy);
+//    plain drains every 4 stages, far below its bfloat16 representation
+//    error.
 //    Groups never cross a row block.  Pieces end in C, or in a partial sum
 //    for the same deterministic stream-K fix-up as the CUDA-core kernels.
 // Every wait is bounded; TMEM is always released before the block exits.
@@ -50,44 +53,42 @@ namespace {
 constexpr int kMM = 128;          // MMA M = TMEM lanes
 constexpr int kSub = 4;           // MMA row tiles per unit
 constexpr int kBM = kSub * kMM;   // 512 rows per unit: 1 KB contiguous per column of A
-constexpr int kKC = 16;           // C columns = MMA N
+constexpr int kKC = 16;           // C columns per B piece
 constexpr int kMaxStages = 8;     // stages are sized at run time: 3 (plain and hi+lo)
-constexpr int kPieces = 3;        // bfloat16 pieces of B
-// Per-stage geometry for BK inner columns per stage.
-template <int BK_>
-struct Depth {
-    static constexpr int BK = BK_;
-    static constexpr int KSteps = BK / 16;                   // MMA K steps per stage
-    static constexpr int Box = 64 * BK * 2;                  // one 64-row TMA box
-    static constexpr int ATile = kBM * BK * 2;               // one A tile (8 boxes)
-    static constexpr int BBlock = kPieces * KSteps * 512;    // B pieces per stage
+constexpr int kMaxBuf = 4;        // TMEM accumulator buffers at most
+constexpr int kTmemCols = 512;    // TMEM columns allocated per block
+// Per-variant geometry: plain A (one bfloat16 matrix) or hi+lo (two).
+template <bool HILO>
+struct Variant {
+    static constexpr int BK = HILO ? 32 : 64;                 // inner columns per stage
+    static constexpr int KSteps = BK / 16;                    // MMA K steps per stage
+    static constexpr int NP = HILO ? 3 : 2;                   // B pieces per MMA (N = 16 NP)
+    static constexpr int Box = 64 * BK * 2;                   // one 64-row TMA box
+    static constexpr int ATile = kBM * BK * 2;                // one A tile (8 boxes)
+    static constexpr int BBlock = KSteps * NP * 512;          // B pieces per stage
+    static constexpr int Stage = (HILO ? 2 : 1) * ATile + BBlock;
+    static constexpr int SubCols = NP * kKC;                  // TMEM columns per row tile
+    static constexpr int BufCols = kSub * SubCols;            // TMEM columns per buffer
+    static constexpr int NBuf = HILO ? 2 : 4;
+    // Instruction descriptor, kind::f16: D f32, A bf16, B bf16, A MN-major
+    // (column-major A: rows contiguous), B K-major, N = 16 NP, M = 128.
+    static constexpr uint32_t Idesc = (1u << 4)               // D format f32
+                                      | (1u << 7)             // A format bf16
+                                      | (1u << 10)            // B format bf16
+                                      | (1u << 15)            // A major: MN
+                                      | (0u << 16)            // B major: K
+                                      | ((uint32_t)(SubCols >> 3) << 17)
+                                      | ((uint32_t)(kMM >> 4) << 24);
+    static_assert(NBuf <= kMaxBuf && NBuf * BufCols <= kTmemCols, "TMEM buffers");
+    static_assert(Stage % 1024 == 0 && Box % 1024 == 0, "1 KB alignment of A boxes");
 };
-constexpr int kBKPlain = 64;
-constexpr int kBKHiLo = 32;
-using DPlain = Depth<kBKPlain>;
-using DHiLo = Depth<kBKHiLo>;
-constexpr int kStagePlain = DPlain::ATile + DPlain::BBlock;    // 70 KB
-constexpr int kStageHiLo = 2 * DHiLo::ATile + DHiLo::BBlock;   // 67 KB
-constexpr int kNBuf = 4;                               // TMEM accumulator buffers
-constexpr int kBufCols = kSub * kKC;                   // 64 columns per buffer
-constexpr int kTmemCols = kNBuf * kBufCols;            // 256 columns
+using VPlain = Variant<false>;
+using VHiLo = Variant<true>;
 constexpr int kSmemBudget = 210 * 1024;                // ring bytes (barriers follow)
-static_assert(kSmemBudget / kStageHiLo >= 3 && kSmemBudget / kStagePlain >= 3 &&
+static_assert(kSmemBudget / VHiLo::Stage >= 3 && kSmemBudget / VPlain::Stage >= 3 &&
                   kSmemBudget + 1024 + 512 <= 227 * 1024,
               "shared memory budget");
-static_assert(kStageHiLo % 1024 == 0 && kStagePlain % 1024 == 0 && DPlain::Box % 1024 == 0 &&
-                  DHiLo::Box % 1024 == 0,
-              "1 KB alignment of A boxes");
 
-// Instruction descriptor, kind::f16: D f32, A bf16, B bf16, A MN-major
-// (column-major A: rows contiguous), B K-major, N = 16, M = 128.
-constexpr uint32_t kIdesc = (1u << 4)          // D format f32
-                            | (1u << 7)        // A format bf16
-                            | (1u << 10)       // B format bf16
-                            | (1u << 15)       // A major: MN
-                            | (0u << 16)       // B major: K
-                            | ((kKC >> 3) << 17)
-                            | ((kMM >> 4) << 24);
 
 // Shared-memory matrix descriptor (tcgen05): start address, leading and
 // stride byte offsets (all >> 4), fixed version 1 (bits 46-47), layout type
@@ -101,12 +102,13 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     return d;
 }
 
-__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -150,7 +152,6 @@ struct BParams {
     int64_t wait_ns;
     int64_t upr;     // stages per row block
     int64_t ngroups; // units in total
-    int hilo;
     int group;        // stages summed in TMEM per drain (1 for hi+lo)
     int stages;       // ring depth
     int stage_bytes;  // ring stride (A_hi, [A_lo], B pieces)
@@ -158,18 +159,18 @@ struct BParams {
 
 __device__ __forceinline__ int64_t owner_b(int64_t x, int64_t G, int64_t NG) { return ((x + 1) * G + NG - 1) / NG - 1; }
 
-template <int BK>
+template <bool HILO>
 __global__ void __launch_bounds__(192, 1)
 bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ CUtensorMap mapLo, const BParams p) {
-    using D = Depth<BK>;
+    using D = Variant<HILO>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = smem_aligned<1024>(smem_raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kSmemBudget);
     uint64_t *full = bars;                   // [stages] TMA landed
     uint64_t *empty = bars + kMaxStages;     // [stages] MMAs done with the stage
-    uint64_t *accf = bars + 2 * kMaxStages;  // [kNBuf] stage sum complete in TMEM
-    uint64_t *acce = accf + kNBuf;           // [kNBuf] drained by the epilogue
-    uint64_t *fin = acce + kNBuf;            // [1] all MMAs finished
+    uint64_t *accf = bars + 2 * kMaxStages;  // [NBuf] stage sum complete in TMEM
+    uint64_t *acce = accf + kMaxBuf;         // [NBuf] drained by the epilogue
+    uint64_t *fin = acce + kMaxBuf;          // [1] all MMAs finished
     const int nst = p.stages;
     const int sbytes = p.stage_bytes;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
@@ -188,7 +189,7 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < kNBuf; ++b) {
+        for (int b = 0; b < D::NBuf; ++b) {
             mbar_init(&accf[b], 1);
             mbar_init(&acce[b], 4);
         }
@@ -212,9 +213,9 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
         // ---------------- producer ----------------
         if (lane == 0) {
             prefetch_tensormap(&mapHi);
-            if (p.hilo) prefetch_tensormap(&mapLo);
+            if (HILO) prefetch_tensormap(&mapLo);
             const uint64_t policy = l2_policy_evict_first();
-            const uint32_t tx = (uint32_t)((p.hilo ? 2 : 1) * D::ATile + D::BBlock);
+            const uint32_t tx = (uint32_t)D::Stage;
             int s = 0;
             uint32_t ph = 0, issued = 0, last_par = 0;
             int rb = (int)(u_begin / p.upr);
@@ -228,11 +229,11 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
                 }
                 unsigned char *st = smem + s * sbytes;
                 mbar_arrive_expect_tx(&full[s], tx);
-                const int32_t x0 = rb * kBM, y0 = kc * BK;
+                const int32_t x0 = rb * kBM, y0 = kc * D::BK;
 #pragma unroll
                 for (int q = 0; q < kBM / 64; ++q) {
                     tma_load_2d_hint(st + q * D::Box, &mapHi, x0 + q * 64, y0, &full[s], policy);
-                    if (p.hilo)
+                    if (HILO)
                         tma_load_2d_hint(st + D::ATile + q * D::Box, &mapLo, x0 + q * 64, y0, &full[s], policy);
                 }
                 bulk_g2s(st + sbytes - D::BBlock, p.bpieces + (size_t)kc * D::BBlock, D::BBlock, &full[s]);
@@ -277,27 +278,18 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
                 const uint32_t st = smem_u32(smem + s * sbytes);
 #pragma unroll
                 for (int ks = 0; ks < D::KSteps; ++ks) {
-                    // B pieces: K-major, no swizzle: K-halves 128 B apart (LBO),
-                    // 8-column groups of C 256 B apart (SBO).
-                    const uint32_t bb = st + sbytes - D::BBlock + ks * 512;
-                    const uint64_t b1 = sdesc(bb, 128, 256, 0);
-                    const uint64_t b2 = sdesc(bb + D::KSteps * 512, 128, 256, 0);
-                    const uint64_t b3 = sdesc(bb + 2 * D::KSteps * 512, 128, 256, 0);
+                    // B pieces of K step ks side by side in N: K-major, no
+                    // swizzle, K-halves 128 B apart (LBO), 8-column groups
+                    // 256 B apart (SBO); piece p covers N = 16p .. 16p + 15.
+                    const uint64_t bdesc = sdesc(st + sbytes - D::BBlock + ks * D::NP * 512, 128, 256, 0);
 #pragma unroll
                     for (int sub = 0; sub < kSub; ++sub) {
                         // A row tile sub: MN-major SW128, its two 64-row boxes
                         // one box apart (LBO), 8-column groups 1 KB apart (SBO).
                         const uint32_t aoff = sub * 2 * D::Box + ks * 2048;
-                        const uint64_t ahi = sdesc(st + aoff, D::Box, 1024, 2);
-                        const uint64_t alo = sdesc(st + D::ATile + aoff, D::Box, 1024, 2);
-                        const uint32_t d = tmem + (uint32_t)(buf * kBufCols + sub * kKC);
-                        umma_f16(d, ahi, b1, (gstart && ks == 0) ? 0u : 1u);
-                        umma_f16(d, ahi, b2, 1u);
-                        if (p.hilo) {
-                            umma_f16(d, ahi, b3, 1u);
-                            umma_f16(d, alo, b1, 1u);
-                            umma_f16(d, alo, b2, 1u);
-                        }
+                        const uint32_t d = tmem + (uint32_t)(buf * D::BufCols + sub * D::SubCols);
+                        umma_f16(d, sdesc(st + aoff, D::Box, 1024, 2), bdesc, D::Idesc, (gstart && ks == 0) ? 0u : 1u);
+                        if (HILO) umma_f16(d, sdesc(st + D::ATile + aoff, D::Box, 1024, 2), bdesc, D::Idesc, 1u);
                     }
                 }
                 issued_any = true;
@@ -305,7 +297,7 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
                 if (gend) {
                     umma_commit(&accf[buf]);  // and the group's sum is ready for the epilogue
                     acc_ph ^= 1u << buf;
-                    if (++buf == kNBuf) buf = 0;
+                    if (++buf == D::NBuf) buf = 0;
                     gcnt = 0;
                 } else {
                     ++gcnt;
@@ -330,8 +322,8 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
         int rb = (int)(u_begin / p.upr);
         int kc = (int)(u_begin - (int64_t)rb * p.upr);
         bool piece_at_start = (kc == 0);
-        // The tensor cores sum 16-term products over one stage only; the long
-        // sum over stages runs here in binary32 with round-to-nearest adds.
+        // The tensor cores sum one group of stages only; the long sum over
+        // groups runs here in binary32 with round-to-nearest adds.
         float v[kSub][kKC];
 #pragma unroll
         for (int sub = 0; sub < kSub; ++sub)
@@ -355,23 +347,35 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
                 }
                 if (!aborted) {
                     tc_fence_after();
-                    // All four row tiles' loads in flight together, one wait.
-                    uint32_t t[kSub][16];
+                    // Two row tiles' pieces in flight per wait; the pieces of
+                    // each output are added smallest first.
 #pragma unroll
-                    for (int sub = 0; sub < kSub; ++sub)
-                        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * kBufCols + sub * kKC),
-                                  t[sub]);
-                    tmem_ld_wait();
+                    for (int sub0 = 0; sub0 < kSub; sub0 += 2) {
+                        uint32_t t[2][D::NP][16];
 #pragma unroll
-                    for (int sub = 0; sub < kSub; ++sub)
+                        for (int h = 0; h < 2; ++h)
 #pragma unroll
-                        for (int c = 0; c < kKC; ++c) v[sub][c] += __uint_as_float(t[sub][c]);
+                            for (int pc = 0; pc < D::NP; ++pc)
+                                tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) +
+                                              (uint32_t)(buf * D::BufCols + (sub0 + h) * D::SubCols + pc * kKC),
+                                          t[h][pc]);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+#pragma unroll
+                            for (int c = 0; c < kKC; ++c) {
+                                float x = __uint_as_float(t[h][D::NP - 1][c]);
+#pragma unroll
+                                for (int pc = D::NP - 2; pc >= 0; --pc) x += __uint_as_float(t[h][pc][c]);
+                                v[sub0 + h][c] += x;
+                            }
+                    }
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&acce[buf]);
                 }
                 acc_ph ^= 1u << buf;
-                if (++buf == kNBuf) buf = 0;
+                if (++buf == D::NBuf) buf = 0;
                 gcnt = 0;
             } else {
                 ++gcnt;
@@ -453,21 +457,23 @@ bf16_kernel(const __grid_constant__ CUtensorMap mapHi, const __grid_constant__ C
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-// Split binary32 B (n x k, k <= 16) into three bfloat16 pieces, written in the
-// MMA B-operand layout [n/bk blocks][piece][kstep][core nb][core kb][8][8]
-// (bk inner columns per block, one block per pipeline stage).
+// Split binary32 B (n x k, k <= 16) into bfloat16 pieces b1 + b2 + b3 = b
+// (each the round-to-nearest-even of the remainder), the first np of them
+// written in the MMA B-operand layout [n/bk blocks][kstep][piece][core nb]
+// [core kb][8][8] (bk inner columns per block, one block per pipeline stage;
+// the pieces of one K step side by side form one N = 16 np operand).
 __global__ void bsplit_kernel(int64_t n, int k, const float *__restrict__ B, int64_t ldb, __nv_bfloat16 *out,
-                              int64_t nblocks, int bk) {
+                              int64_t nblocks, int bk, int np) {
     const int ksteps = bk / 16;
-    const int64_t total = nblocks * kPieces * ksteps * 256;  // bf16 elements
+    const int64_t total = nblocks * ksteps * np * 256;  // bf16 elements
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         int64_t q = t;
         const int e = (int)(q % 8); q /= 8;
         const int rr = (int)(q % 8); q /= 8;
         const int kb = (int)(q % 2); q /= 2;
         const int nb = (int)(q % 2); q /= 2;
+        const int piece = (int)(q % np); q /= np;
         const int ks = (int)(q % ksteps); q /= ksteps;
-        const int piece = (int)(q % kPieces); q /= kPieces;
         const int64_t blk = q;
         const int64_t j = blk * bk + ks * 16 + kb * 8 + e;
         const int c = nb * 8 + rr;
@@ -530,23 +536,25 @@ __global__ void split_kernel(int64_t rows, int64_t cols, const float *X, int64_t
 }  // namespace
 
 int bf16_bm() { return kBM; }
-int bf16_bk(bool hilo) { return hilo ? kBKHiLo : kBKPlain; }
+int bf16_bk(bool hilo) { return hilo ? VHiLo::BK : VPlain::BK; }
 size_t bf16_bpieces_bytes(int64_t n, bool hilo) {
     const int bk = bf16_bk(hilo);
-    return (size_t)((n + bk - 1) / bk) * (hilo ? DHiLo::BBlock : DPlain::BBlock);
+    return (size_t)((n + bk - 1) / bk) * (hilo ? VHiLo::BBlock : VPlain::BBlock);
 }
 
 cudaError_t bf16_prep_b(int64_t n, int k, const float *B, int64_t ldb, void *out, bool hilo, cudaStream_t stream) {
     const int bk = bf16_bk(hilo);
     const int64_t nblocks = (n + bk - 1) / bk;
-    const int64_t total = nblocks * kPieces * (bk / 16) * 256;
+    const int np = hilo ? VHiLo::NP : VPlain::NP;
+    const int64_t total = nblocks * (bk / 16) * np * 256;
     int64_t grid = (total + 255) / 256;
     if (grid > 4096) grid = 4096;
-    bsplit_kernel<<<(unsigned)grid, 256, 0, stream>>>(n, k, B, ldb, static_cast<__nv_bfloat16 *>(out), nblocks, bk);
+    bsplit_kernel<<<(unsigned)grid, 256, 0, stream>>>(n, k, B, ldb, static_cast<__nv_bfloat16 *>(out), nblocks, bk,
+                                                      np);
     return cudaGetLastError();
 }
 
-template <int BK>
+template <bool HILO>
 cudaError_t bf16_set_smem(int smem) {
     static std::mutex mu;
     static uint64_t attr_done = 0;  // one bit per device
@@ -555,7 +563,7 @@ cudaError_t bf16_set_smem(int smem) {
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(mu);
     if (dev < 64 && !(attr_done & (1ull << dev))) {
-        e = cudaFuncSetAttribute(bf16_kernel<BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(bf16_kernel<HILO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_done |= 1ull << dev;
     }
@@ -564,7 +572,7 @@ cudaError_t bf16_set_smem(int smem) {
 
 cudaError_t bf16_launch(const BF16Launch &L, cudaStream_t stream) {
     const int smem = kSmemBudget + 1024 + 512;  // ring + 1 KB alignment slack + barriers
-    cudaError_t e = L.hilo ? bf16_set_smem<kBKHiLo>(smem) : bf16_set_smem<kBKPlain>(smem);
+    cudaError_t e = L.hilo ? bf16_set_smem<true>(smem) : bf16_set_smem<false>(smem);
     if (e != cudaSuccess) return e;
     BParams p;
     p.m = L.m;
@@ -580,18 +588,17 @@ cudaError_t bf16_launch(const BF16Launch &L, cudaStream_t stream) {
     const int bk = bf16_bk(L.hilo);
     p.upr = (L.n + bk - 1) / bk;
     p.ngroups = ((L.m + kBM - 1) / kBM) * p.upr;
-    p.hilo = L.hilo ? 1 : 0;
     // Plain: the tensor cores sum 4 stages (256 inner indices, 512 products
     // per output) before each drain, far inside the bfloat16 representation
     // error of A; hi+lo: one stage per drain, for binary32-like accuracy.
     p.group = L.hilo ? 1 : 4;
-    p.stage_bytes = L.hilo ? kStageHiLo : kStagePlain;
+    p.stage_bytes = L.hilo ? VHiLo::Stage : VPlain::Stage;
     p.stages = kSmemBudget / p.stage_bytes;
     if (p.stages > kMaxStages) p.stages = kMaxStages;
     if (L.hilo)
-        bf16_kernel<kBKHiLo><<<L.grid, 192, smem, stream>>>(L.mapHi, L.mapLo, p);
+        bf16_kernel<true><<<L.grid, 192, smem, stream>>>(L.mapHi, L.mapLo, p);
     else
-        bf16_kernel<kBKPlain><<<L.grid, 192, smem, stream>>>(L.mapHi, L.mapLo, p);
+        bf16_kernel<false><<<L.grid, 192, smem, stream>>>(L.mapHi, L.mapLo, p);
     return cudaGetLastError();
 }
 
