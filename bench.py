@@ -622,6 +622,7 @@ def run_gpu(args):
     if not args.no_crossover:
         rows_x = []
         worst = 1.0
+        picked = 0
         for m in (15360, 1 << 20):
             for n in (4, 16, 64, 256, 1024):
                 k = 16
@@ -648,14 +649,20 @@ def run_gpu(args):
                     ms = statistics.median(ts)
                     rec[name] = {"gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), "config": pkg.tsm2_last_config()}
                 best = max(rec["tsm2r"]["gbs"], rec["tsm2l"]["gbs"])
+                best_op = "tsm2r" if rec["tsm2r"]["gbs"] >= rec["tsm2l"]["gbs"] else "tsm2l"
                 rec["tsm2x_over_best"] = round(rec["tsm2x"]["gbs"] / best, 3)
+                # The choice itself, free of timing noise on the small cases:
+                # TSM2X ran the configuration of the faster schedule.
+                rec["tsm2x_picked_faster"] = rec["tsm2x"]["config"] == rec[best_op]["config"]
+                picked += int(rec["tsm2x_picked_faster"])
                 worst = min(worst, rec["tsm2x_over_best"])
                 rows_x.append(rec)
                 del A, B, C
         pkg.check(pkg.tsm2_get_device_status(sh))
         crossover = {"workload": "binary32 A m x n (m in {15360, 2^20}, inner n in {4..1024}), B n x 16, "
                                  "uniform[-1,1) seed 0; TSM2R vs TSM2L (B resident n <= 64, staged above) vs the "
-                                 "TSM2X choice", "worst_tsm2x_over_best": worst, "cases": rows_x}
+                                 "TSM2X choice", "worst_tsm2x_over_best": worst,
+                     "tsm2x_picked_faster": f"{picked}/{len(rows_x)}", "cases": rows_x}
 
     # ---- CPU oracle baseline (rank 0, N = 1) --------------------------------------------------
     cpu = None
