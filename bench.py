@@ -170,6 +170,24 @@ def dist_setup():
     return world, rank, local
 
 
+def ranks_max(x, dev, world):
+    """Largest value of x over all ranks (a step time: the slowest rank sets
+    the job's time).  One rank: x itself, no collective."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(world, step_bytes, ms):
+    """Whole-job throughput: every rank moves step_bytes per step (weak
+    scaling, replicas), the step takes the slowest rank's ms."""
+    return world * step_bytes / (ms * 1e-3) / 1e9
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle arm (reference arm and cpu_baseline)
 
@@ -323,13 +341,9 @@ def run_gpu(args):
     per, configs, wall = timed_steps(work32, args.steps, args.warmup)
     clock_rec = clocks.stop()
     step_ms = [sum(row) for row in per]
-    mean_step_ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([mean_step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mean_step_ms = float(t.item())
+    mean_step_ms = ranks_max(statistics.mean(step_ms), dev, world)
     step_bytes = sum(w["bytes"] for w in work32)
-    value = world * step_bytes / (mean_step_ms * 1e-3) / 1e9
+    value = job_gbs(world, step_bytes, mean_step_ms)
     case_rows = []
     for i, w in enumerate(work32):
         ms = statistics.mean(per[s][i] for s in range(args.steps))
@@ -386,12 +400,8 @@ def run_gpu(args):
         e2e_step()
     e_end.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e_start.elapsed_time(e_end) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": round(world * step_bytes / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+    e2e_ms = ranks_max(e_start.elapsed_time(e_end) / e2e_steps, dev, world)
+    e2e = {"value": round(job_gbs(world, step_bytes, e2e_ms), 2), "unit": "GB/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)}
     del h_in, h_out, h_shared
 
