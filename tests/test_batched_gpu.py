@@ -107,3 +107,53 @@ def test_autotuner_picks_a_valid_plan(tmp_path):
     assert rec2.get("cached") and rec2["flags"] == rec["flags"]
     plan.close()
     plan2.close()
+
+
+@pytest.mark.parametrize("flags,serial", [(1, True), (0, False)])
+def test_batch_fullsize_workload_sampled(flags, serial):
+    """The benchmark's 512-problem workload (256 TSM2R n^2 x k, n in [512,
+    8192]; 256 TSM2L, m in [2^14, 2^20], n = k in 4..32; about 43 GB of A and
+    C), inputs generated on the device exactly as the benchmark makes them,
+    one CUDA-graph launch of the plan; sampled rows of every fourth problem
+    (128 of them, across the classes) against the oracle on rows regenerated
+    on the host, and every entry of every C finite."""
+    import paper_2002_03258_gb300 as pkg
+    import paper_2002_03258_gb300.batched as bt
+    lib = pkg.lib()
+    shapes = ti.batch_shapes(0)
+    probs, bufs = [], []
+    for idx, (op, m, n, k) in enumerate(shapes):
+        lda = (m + 3) // 4 * 4
+        ldb = (n + 3) // 4 * 4
+        tA = torch.empty((n, lda), dtype=torch.float32, device="cuda")
+        tB = torch.empty((k, ldb), dtype=torch.float32, device="cuda")
+        tC = torch.full((k, lda), float("nan"), dtype=torch.float32, device="cuda")
+        assert lib.tsm2_fill_uniform_s(m, n, idx, ti.MID_A, tA.data_ptr(), lda, 0) == 0
+        assert lib.tsm2_fill_uniform_s(n, k, idx, ti.MID_B, tB.data_ptr(), ldb, 0) == 0
+        bufs.append((tA, tB, tC))
+        probs.append(bt.problem(op, m, n, k, tA.data_ptr(), lda, tB.data_ptr(), ldb, tC.data_ptr(), lda))
+    plan = bt.BatchPlan(probs, flags)
+    plan.set_serial(serial)
+    plan.graph_launch(0)
+    assert pkg.tsm2_get_device_status(0) == 0
+    # every fourth problem of the (shuffled) batch, 10 random rows plus the
+    # first and the last
+    rng = np.random.default_rng(11)
+    checked = 0
+    for idx, (op, m, n, k) in enumerate(shapes):
+        if idx % 4:
+            continue
+        tA, tB, tC = bufs[idx]
+        rows = np.unique(np.concatenate([rng.integers(0, m, 10), [0, m - 1]]))
+        got = tC.t()[torch.from_numpy(rows).cuda(), :k].cpu().numpy()
+        A_rows = ti.uniform_pm1(idx, ti.MID_A, m, n, np.float32, row_idx=rows)
+        B = ti.uniform_pm1(idx, ti.MID_B, n, k, np.float32)
+        assert_parity(got, A_rows, B, np.float32)
+        checked += 1
+    assert checked == 128
+    # whole-C property at any size: every C entry of every problem finite
+    for (tA, tB, tC), (op, m, n, k) in zip(bufs, shapes):
+        assert bool(torch.isfinite(tC.t()[:m, :k]).all()), (op, m, n, k)
+    plan.close()
+    del bufs
+    torch.cuda.empty_cache()
