@@ -220,7 +220,8 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
                     // wide accumulator tiles.
                     if (whole) {
                         T *cw = C + row0 + (int64_t)kbase * ldc;
-                        const bool fast = pd->c_vec && row0 + K::BM <= m && kbase + K::KCW <= kk;
+                        const bool vrows = pd->c_vec && row0 + K::BM <= m;  // whole 16-byte row vectors
+                        const bool fast = vrows && kbase + K::KCW <= kk;
                         if (fast) {
 #pragma unroll
                             for (int c = 0; c < K::KCW; ++c) {
@@ -230,6 +231,21 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
 #pragma unroll
                                     for (int e = 0; e < K::V; ++e) tmp[e] = acc[v * K::V + e][c];
                                     *reinterpret_cast<vec_t *>(cw + row_of(v)) = K::VT::make(tmp);
+                                }
+                                cw += ldc;
+                            }
+                        } else if (vrows) {
+                            // Columns past k skipped, rows still whole vectors.
+#pragma unroll
+                            for (int c = 0; c < K::KCW; ++c) {
+                                if (kbase + c < kk) {
+#pragma unroll
+                                    for (int v = 0; v < K::NV; ++v) {
+                                        T tmp[K::V];
+#pragma unroll
+                                        for (int e = 0; e < K::V; ++e) tmp[e] = acc[v * K::V + e][c];
+                                        *reinterpret_cast<vec_t *>(cw + row_of(v)) = K::VT::make(tmp);
+                                    }
                                 }
                                 cw += ldc;
                             }

@@ -297,7 +297,8 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                     {
                         // Fast path: the row block lies inside C, all its columns are
                         // live and C allows 16-byte stores: unpredicated vector stores.
-                        const bool fast = p.c_vec && row0 + K::BM <= p.m && kbase + K::KCW <= p.k;
+                        const bool vrows = p.c_vec && row0 + K::BM <= p.m;  // whole 16-byte row vectors
+                        const bool fast = vrows && kbase + K::KCW <= p.k;
                         const int64_t ldc = *s_ldc;
                         T *cw = C + row0 + (int64_t)kbase * ldc;
                         if (fast) {
@@ -309,6 +310,21 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 #pragma unroll
                                     for (int e = 0; e < K::V; ++e) tmp[e] = acc[v * K::V + e][c];
                                     *reinterpret_cast<vec_t *>(cw + row_of(v)) = K::VT::make(tmp);
+                                }
+                                cw += ldc;
+                            }
+                        } else if (vrows) {
+                            // Columns past k skipped, rows still whole vectors.
+#pragma unroll
+                            for (int c = 0; c < K::KCW; ++c) {
+                                if (kbase + c < p.k) {
+#pragma unroll
+                                    for (int v = 0; v < K::NV; ++v) {
+                                        T tmp[K::V];
+#pragma unroll
+                                        for (int e = 0; e < K::V; ++e) tmp[e] = acc[v * K::V + e][c];
+                                        *reinterpret_cast<vec_t *>(cw + row_of(v)) = K::VT::make(tmp);
+                                    }
                                 }
                                 cw += ldc;
                             }
