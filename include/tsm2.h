@@ -132,8 +132,9 @@ tsm2_status tsm2_rankk_s(int64_t m, int64_t n, int64_t k, const float *dC, int64
  * tsm2_split_bf16); NULL means A = A_hi.  The paper omits half precision
  * (Sec. 4.1); this extends TSM2R (Sec. 3.1): A is streamed once, at half the
  * bytes of binary32 (or the same bytes, with about 16 significant bits, for
- * hi + lo), and the products run on the tensor cores (B is split exactly into
- * three bfloat16 pieces internally).  Error: |C - A_hi B| <= about
+ * hi + lo), and the products run on the tensor cores (B is split internally
+ * into bfloat16 pieces b1 + b2 + b3 = b exactly; plain A uses b1 + b2, B to
+ * about 16 bits, hi + lo all three).  Error: |C - A_hi B| <= about
  * (2^-18 + 2 n 2^-23) |A_hi||B| (plain), |C - (A_hi + A_lo) B| <= about
  * (2^-27 + 5 n 2^-23) |A||B| (hi + lo).  The bulk-copy path needs 16-byte
  * aligned A_hi/A_lo and lda a multiple of 8; otherwise an element-wise
