@@ -761,6 +761,57 @@ def run_case(args):
     return 0
 
 
+def run_batch_case(args):
+    """One tile class of the batched workload: the first `count` problems of
+    the 512-problem batch whose op is `op` and whose k chunk uses the C-column
+    width `kc`, as one plan (flags), executed like the batched leg (for the
+    ncu captures of the batched kernel)."""
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2002_03258_gb300 as pkg
+    import paper_2002_03258_gb300.batched as bt
+    import tsm2_inputs as ti
+    op, kc, count, flags = args.batch_case.split(":")
+    kc, count, flags = int(kc), int(count), int(flags)
+    widths = (2, 4, 8, 12, 16, 24, 32)
+    lib = pkg.lib()
+    probs, keep, total = [], [], 0
+    for idx, (o, m, n, k) in enumerate(ti.batch_shapes(0)):
+        if o != op or next(w for w in widths if w >= min(k, 32 if o == "l" else 16)) != kc or len(probs) >= count:
+            continue
+        lda, ldb = (m + 3) // 4 * 4, (n + 3) // 4 * 4
+        tA = torch.empty((n, lda), dtype=torch.float32, device="cuda")
+        tB = torch.empty((k, ldb), dtype=torch.float32, device="cuda")
+        tC = torch.empty((k, lda), dtype=torch.float32, device="cuda")
+        pkg.check(lib.tsm2_fill_uniform_s(m, n, idx, ti.MID_A, tA.data_ptr(), lda, 0))
+        pkg.check(lib.tsm2_fill_uniform_s(n, k, idx, ti.MID_B, tB.data_ptr(), ldb, 0))
+        keep += [tA, tB, tC]
+        probs.append(bt.problem(o, m, n, k, tA.data_ptr(), lda, tB.data_ptr(), ldb, tC.data_ptr(), lda))
+        total += 4 * (m * n + n * k + m * k)
+    plan = bt.BatchPlan(probs, flags)
+    l2 = getattr(torch.cuda.get_device_properties(0), "L2_cache_size", 128 << 20) or (128 << 20)
+    flush = torch.empty(2 * l2, dtype=torch.uint8, device="cuda")
+    ts = []
+    for r in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.execute(0)
+        e1.record()
+        torch.cuda.synchronize()
+        if r >= args.warmup:
+            ts.append(e0.elapsed_time(e1))
+    pkg.check(pkg.tsm2_get_device_status(0))
+    ms = statistics.median(ts)
+    print(json.dumps({"batch_case": args.batch_case, "problems": len(probs), "classes": [c["name"] for c in plan.classes()],
+                      "ms": round(ms, 4), "gbs": round(total / (ms * 1e-3) / 1e9, 1), "algorithmic_bytes": total}),
+          flush=True)
+    plan.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -776,9 +827,13 @@ def main():
     ap.add_argument("--no-crossover", action="store_true")
     ap.add_argument("--case", default=None, help="op:dtype:m:n:k, e.g. r:f32:8192:8192:16 -- time one multiply only (op r, l or x; dtype "
                          "f32, f64, or for op r bf16 / bf16hilo)")
+    ap.add_argument("--batch-case", default=None, help="op:kc:count:flags, e.g. l:32:20:1 -- time one tile class of the "
+                    "batched workload (its first `count` problems) as one plan")
     args = ap.parse_args()
     if args.case:
         return run_case(args)
+    if args.batch_case:
+        return run_batch_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -87,18 +87,25 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
             int pi = pi0;
             const ProbDesc *pd = &p.probs[pi];
             int64_t next_begin = (pi + 1 < p.nprob) ? p.probs[pi + 1].group_begin : p.ngroups;
+            // Row block and stage of the current unit, stepped unit by unit;
+            // the descriptor is read again only at a change of problem.
+            int upr = pd->upr, gran = pd->gran;
+            int rb = (int)(gs - pd->group_begin) * gran / upr;
+            int jc = (int)(gs - pd->group_begin) * gran - rb * upr;
             bool stop = false;
             for (int64_t gg = gs; gg < ge && !stop; ++gg) {
-                while (gg >= next_begin) {
-                    ++pi;
+                if (gg >= next_begin) {  // the next non-empty problem, from its first unit
+                    do {
+                        ++pi;
+                        next_begin = (pi + 1 < p.nprob) ? p.probs[pi + 1].group_begin : p.ngroups;
+                    } while (gg >= next_begin);
                     pd = &p.probs[pi];
-                    next_begin = (pi + 1 < p.nprob) ? p.probs[pi + 1].group_begin : p.ngroups;
+                    upr = pd->upr;
+                    gran = pd->gran;
+                    rb = 0;
+                    jc = 0;
                 }
-                const int upr = pd->upr, gran = pd->gran;
-                const int lg = (int)(gg - pd->group_begin);
                 for (int t = 0; t < gran; ++t) {
-                    const int unit = lg * gran + t;
-                    const int rb = unit / upr, jc = unit - (unit / upr) * upr;
                     if (flags[0] || !mbar_wait_bounded(&empty[s], ph ^ 1u, p.wait_ns, flags)) {
                         flags[0] = 1;
                         atomicOr(p.status, kStatusTimeout);
@@ -116,6 +123,7 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
                     issued |= 1u << s;
                     last_par = (last_par & ~(1u << s)) | (ph << s);
                     if (++s == K::STAGES) { s = 0; ph ^= 1u; }
+                    if (++jc == upr) { jc = 0; ++rb; }
                 }
             }
             for (int t = 0; t < K::STAGES; ++t)
@@ -146,11 +154,20 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
     const ProbDesc *pd = &p.probs[pi];
     int64_t next_begin = (pi + 1 < p.nprob) ? p.probs[pi + 1].group_begin : p.ngroups;
     bool load_b = true;
+    int upr = pd->upr, gran = pd->gran;  // see the producer: stepped, not recomputed
+    int rb = (int)(gs - pd->group_begin) * gran / upr;
+    int jc = (int)(gs - pd->group_begin) * gran - rb * upr;
     for (int64_t gg = gs; gg < ge; ++gg) {
-        while (gg >= next_begin) {  // next problem
-            ++pi;
+        if (gg >= next_begin) {  // the next non-empty problem, from its first unit
+            do {
+                ++pi;
+                next_begin = (pi + 1 < p.nprob) ? p.probs[pi + 1].group_begin : p.ngroups;
+            } while (gg >= next_begin);
             pd = &p.probs[pi];
-            next_begin = (pi + 1 < p.nprob) ? p.probs[pi + 1].group_begin : p.ngroups;
+            upr = pd->upr;
+            gran = pd->gran;
+            rb = 0;
+            jc = 0;
             load_b = true;
         }
         if constexpr (K::BRES) {
@@ -163,11 +180,7 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
             }
         }
         load_b = false;
-        const int upr = pd->upr, gran = pd->gran;
-        const int lg = (int)(gg - pd->group_begin);
         for (int t = 0; t < gran; ++t) {
-            const int unit = lg * gran + t;
-            const int rb = unit / upr, jc = unit - (unit / upr) * upr;
             if (!aborted) {
                 bool ok = !flags[0] && mbar_wait_bounded(&full[s], ph, p.wait_ns, flags);
                 ok = __all_sync(0xffffffffu, ok);
@@ -203,8 +216,10 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
             if (rb_end || last) {
                 // ---- epilogue of one piece of row block rb of problem pi ----
                 const int64_t rb64 = rb;
-                const int64_t rb_g0 = pd->group_begin + (rb64 * upr) / gran;         // first group of rb
-                const int64_t rb_g1 = pd->group_begin + (rb64 * upr + upr - 1) / gran;  // last group of rb
+                // First and last group of rb: a group is one stage (gran 1) or
+                // a whole row block (gran upr).
+                const int64_t rb_g0 = pd->group_begin + (gran == 1 ? rb64 * upr : rb64);
+                const int64_t rb_g1 = pd->group_begin + (gran == 1 ? rb64 * upr + upr - 1 : rb64);
                 const bool whole = (rb_g0 >= gs) && rb_end;
                 const int64_t row0 = rb64 * K::BM;
                 const int64_t m = pd->m;
@@ -337,6 +352,7 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
 #pragma unroll
                     for (int c = 0; c < K::KCW; ++c) acc[r][c] = T(0);
             }
+            if (++jc == upr) { jc = 0; ++rb; }
         }
     }
 }
