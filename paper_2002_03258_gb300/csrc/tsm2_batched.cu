@@ -220,7 +220,10 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
                 // a whole row block (gran upr).
                 const int64_t rb_g0 = pd->group_begin + (gran == 1 ? rb64 * upr : rb64);
                 const int64_t rb_g1 = pd->group_begin + (gran == 1 ? rb64 * upr + upr - 1 : rb64);
-                const bool whole = (rb_g0 >= gs) && rb_end;
+                // TSM2L classes (WC == 1) take whole row blocks only; saying
+                // so at compile time also keeps ptxas from spilling their
+                // wide accumulator tiles.
+                const bool whole = K::WC == 1 || ((rb_g0 >= gs) && rb_end);
                 const int64_t row0 = rb64 * K::BM;
                 const int64_t m = pd->m;
                 const int kk = pd->k;

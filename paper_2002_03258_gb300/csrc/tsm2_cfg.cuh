@@ -283,9 +283,10 @@ template <int KC>
 using W32 = Cfg<float, KC, w32_shape(KC).nv, w32_shape(KC).wr, 1, w32_shape(KC).wk, w32_shape(KC).jw,
                 w32_shape(KC).st, true, 64, (TSM2_L_BT != 0 && (KC / w32_shape(KC).wk) % 4 == 0), 0, false,
                 w32_shape(KC).sepi>;
-// The batched kernel writes C straight from registers: 8 C columns per lane.
+// The batched kernel writes C straight from registers: 16 C columns per lane
+// for KC = 32 (as the single-problem kernel), 8-12 below.
 constexpr WShape w32n_shape(int kc) {
-    return kc >= 32 ? WShape{2, 2, 4, 8, 5, false} : kc >= 16 ? WShape{2, 4, 2, 8, 5, false} : WShape{2, 8, 1, 4, 5, false};
+    return kc >= 16 ? WShape{2, 4, 2, 8, 5, false} : WShape{2, 8, 1, 4, 5, false};
 }
 template <int KC>
 using W32N = Cfg<float, KC, w32n_shape(KC).nv, w32n_shape(KC).wr, 1, w32n_shape(KC).wk, w32n_shape(KC).jw,
