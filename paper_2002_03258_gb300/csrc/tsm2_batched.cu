@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(384, 1) batched_kernel(const BatchParams p) {
                 // Resident B of this problem; every warp finished the previous
                 // problem's last piece (its epilogue) before reaching here.
                 named_bar_sync(1, K::NT);
-                load_resident_b<K>(sBres, static_cast<const T *>(pd->B), pd->n, pd->k, pd->ldb, tid, K::NT);
+                load_resident_b<K>(sBres, static_cast<const T *>(pd->B), pd->n, pd->k, pd->ldb, tid);
                 named_bar_sync(1, K::NT);
             }
         }

@@ -194,17 +194,30 @@ __device__ __forceinline__ void consume_stage(const typename K::T *a_st, const t
     }
 }
 
-// Resident B (n <= NRES inner indices, KC columns) into shared memory, zero
-// beyond n and k so padded lanes contribute exact zeros: column c at
-// sBres[c*NRES + j], or row-major (K::BT) (j, c) at sBres[j*KC + c].
+// Resident B (n <= NRES inner indices, KC columns) into shared memory by the
+// NT consumer threads (tid 0 .. NT-1), zero beyond n and k so padded lanes
+// contribute exact zeros: column c at sBres[c*NRES + j], or row-major
+// (K::BT) (j, c) at sBres[j*KC + c].  All of a thread's loads are issued
+// before its stores, so their DRAM round trips overlap (one after another,
+// the eight loads per thread of KC = 32 delayed the first stage by ~5 us).
 template <class K>
 __device__ __forceinline__ void load_resident_b(typename K::T *sBres, const typename K::T *B, int64_t n, int k,
-                                                int64_t ldb, int tid, int nthreads) {
+                                                int64_t ldb, int tid) {
     using T = typename K::T;
-    for (int t = tid; t < K::KC * K::NRES; t += nthreads) {
+    constexpr int TOTAL = K::KC * K::NRES;
+    constexpr int PER = (TOTAL + K::NT - 1) / K::NT;
+    T v[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int t = tid + i * K::NT;
         const int j = K::BT ? t / K::KC : t % K::NRES;
         const int c = K::BT ? t % K::KC : t / K::NRES;
-        sBres[t] = (j < n && c < k) ? B[j + (int64_t)c * ldb] : T(0);
+        v[i] = (t < TOTAL && j < n && c < k) ? B[j + (int64_t)c * ldb] : T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int t = tid + i * K::NT;
+        if (t < TOTAL) sBres[t] = v[i];
     }
 }
 

@@ -158,7 +158,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     if constexpr (K::BRES) {
         // Whole of B (n <= NRES) once per block, loaded by the consumers
         // while the producer's first copies of A are already in flight.
-        load_resident_b<K>(sBres, static_cast<const T *>(p.B), p.n, p.k, p.ldb, threadIdx.x - 128, K::NT);
+        load_resident_b<K>(sBres, static_cast<const T *>(p.B), p.n, p.k, p.ldb, threadIdx.x - 128);
         named_bar_sync(1, K::NT);
     }
     const int cwarp = warp - 4;                 // consumer warp 0 .. NW-1
