@@ -17,6 +17,7 @@ import hashlib
 import json
 import os
 import statistics
+import tempfile
 
 from .batched import MERGE_L, MERGE_R, WIDE_L, BatchPlan
 
@@ -45,6 +46,37 @@ def shares_from_times(times, sm_count):
     return [1 + int(left * t / tot) for t in times]
 
 
+def load_cache(path):
+    """The tuning cache at `path` as a dict ({} when absent or unreadable)."""
+    if not path or not os.path.exists(path):
+        return {}
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        return {}
+    return cache if isinstance(cache, dict) else {}
+
+
+def store_cache(path, key, rec):
+    """Adds `rec` under `key` to the cache at `path`.  The file is replaced
+    atomically, so a concurrent reader sees the old or the new cache, never a
+    partial one."""
+    cache = load_cache(path)
+    cache[key] = rec
+    d = os.path.dirname(os.path.abspath(path))
+    os.makedirs(d, exist_ok=True)
+    fd, tmp = tempfile.mkstemp(prefix=".tsm2_tune_", suffix=".json", dir=d)
+    try:
+        with os.fdopen(fd, "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(tmp, path)
+    except BaseException:
+        if os.path.exists(tmp):
+            os.unlink(tmp)
+        raise
+
+
 def problem_set_key(problems) -> str:
     h = hashlib.sha256()
     for p in problems:
@@ -61,12 +93,7 @@ def autotune(problems, flags_choices=FLAG_CHOICES, reps=3, flush=None, cache_pat
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     key = f"{props.name}|{problem_set_key(problems)}"
-    cache = {}
-    if cache_path and os.path.exists(cache_path):
-        try:
-            cache = json.load(open(cache_path))
-        except Exception:
-            cache = {}
+    cache = load_cache(cache_path)
     if key in cache:
         rec = cache[key]
         plan = BatchPlan(problems, rec["flags"])
@@ -103,7 +130,5 @@ def autotune(problems, flags_choices=FLAG_CHOICES, reps=3, flush=None, cache_pat
     plan.set_serial(serial)
     rec = {"flags": flags, "grids": grids, "serial": serial, "ms": round(t, 4), "trials": trials}
     if cache_path:
-        cache[key] = {"flags": flags, "grids": grids, "serial": serial, "ms": round(t, 4)}
-        os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
-        json.dump(cache, open(cache_path, "w"), indent=1)
+        store_cache(cache_path, key, {"flags": flags, "grids": grids, "serial": serial, "ms": round(t, 4)})
     return plan, rec
