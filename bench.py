@@ -405,7 +405,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_ms = ranks_max(e_start.elapsed_time(e_end) / e2e_steps, dev, world)
     e2e = {"value": round(job_gbs(world, step_bytes, e2e_ms), 2), "unit": "GB/s",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)}
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3),
+           "host_copy": pkg.tsm2_last_host_copy()}
     del h_in, h_out, h_shared
 
     # ---- cuBLAS comparator on the same operands (not timed in the step) -----------------

@@ -174,6 +174,11 @@ char tsm2x_choice(int elem_bytes, int64_t m, int64_t n, int64_t k);
  *    through two device staging slots; each chunk's C rows are copied back
  *    as soon as its product is done.  Copy-in of the next chunk overlaps the
  *    product and copy-out of the current one.
+ *  - Copies: a buffer in page-locked memory that the device can address
+ *    (cudaHostAlloc / cudaMallocHost, or cudaHostRegister'ed and mapped) is
+ *    read or written by copy kernels on the SMs (24 SMs in, 2-16 out; the
+ *    product kernels then use the remaining SMs); any other buffer is copied
+ *    by the copy engines (cudaMemcpy2DAsync).  See tsm2_set_host_copy.
  *  - Ordering: the work starts after everything already queued on `stream`,
  *    and `stream` waits for the last C rows to reach the host: synchronise
  *    `stream` before reading C.  The host buffers must stay valid until then.
@@ -317,6 +322,11 @@ void tsm2_set_path(int path);
  * SM, limited so each block gets at least a few work units). */
 void tsm2_set_grid(int blocks);
 
+/* How the host-operand entry points move page-locked buffers: 0 = copy
+ * kernels on the SMs where the device can address the buffer (default),
+ * 1 = always the copy engines.  Other values select 0. */
+void tsm2_set_host_copy(int mode);
+
 /* Per-block timeline of the bulk-copy kernels, for profiling.  When set,
  * every later launch whose grid has at most `blocks` blocks writes four
  * 64-bit words per block b into device memory at device_words[4b..4b+3]:
@@ -328,6 +338,11 @@ void tsm2_set_trace(unsigned long long *device_words, int64_t blocks);
 /* Name of the kernel configuration the last call on this thread launched
  * (for reports and tests). */
 const char *tsm2_last_config(void);
+
+/* How the last host-operand call on this thread moved A, B and C: a string
+ * "A:<p> B:<p> C:<p>" with <p> "sm" (copy kernels) or "engine" (copy
+ * engines); "none" before the first such call (for reports and tests). */
+const char *tsm2_last_host_copy(void);
 
 /* ---- Synthetic inputs (definition in tsm2_inputs: splitmix64 counter
  * stream per (seed, matrix_id); element (i,j) of the logical rows x cols

@@ -63,6 +63,14 @@ cudaError_t stream_launch(const StreamShape *shape, const StreamLaunch &L, cudaS
 cudaError_t bt_pack_launch(int elem, int64_t n, int k, const void *B, int64_t ldb, int kc, void *Bt,
                            cudaStream_t stream);
 
+// Copies `cols` columns of `row_bytes` bytes (column c at src + c*lds_bytes,
+// dst + c*ldd_bytes) with the SMs' loads and stores; either side may be a
+// device-mapped address of page-locked host memory.  `grid` blocks, each
+// holding a whole SM.  Requires 4-byte aligned starts and strides and
+// row_bytes % 4 == 0 (cudaErrorInvalidValue otherwise).
+cudaError_t sm_copy2d_launch(const void *src, int64_t lds_bytes, void *dst, int64_t ldd_bytes, int64_t row_bytes,
+                             int64_t cols, int grid, cudaStream_t stream);
+
 // Element-wise fallback (any alignment), Algorithm 3 style.
 cudaError_t simple_launch(int elem, const GemmArgs &g, unsigned *status, cudaStream_t stream);
 int simple_kc_max();

@@ -24,10 +24,13 @@ __device__ unsigned int g_status_word;  // per device; bit kStatusTimeout set by
 
 thread_local std::string t_last_error = "no error";
 thread_local const char *t_last_config = "none";
+thread_local const char *t_last_host_copy = "none";  // copy path of the last host-operand call
 
 int64_t g_wait_ns = 1000000000LL;
 int g_path = 0;
 int g_grid_override = 0;
+int g_host_copy = 0;               // 0: SM copies for device-mapped page-locked host buffers; 1: copy engines
+thread_local int t_grid_cap = 0;   // > 0: upper bound of the product kernels' persistent grid (this thread)
 unsigned long long *g_trace = nullptr;
 int64_t g_trace_blocks = 0;
 
@@ -300,6 +303,7 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
         }
         if (grid > ngroups) grid = ngroups;
         if (g_grid_override > 0) grid = g_grid_override < ngroups ? g_grid_override : ngroups;
+        if (t_grid_cap > 0 && grid > t_grid_cap) grid = t_grid_cap;
         if (grid < 1) grid = 1;
         L.grid = (int)grid;
         void *ws = nullptr;
@@ -829,6 +833,33 @@ char tsm2x_schedule(int elem, int64_t m, int64_t n, int64_t k) {
 // rows.  Copy-in of chunk c+1 overlaps the product and copy-out of chunk c,
 // and copy-in of chunk c+2 waits only for copy-out of chunk c (which itself
 // followed the product), so the link stays busy in both directions.
+//
+// Page-locked buffers that the device can address are copied by SM kernels
+// (tsm2_hostcopy.cu) on kCopyInSMs + up to kCopyOutSMs whole SMs, and the
+// product kernels' grid is capped to the remaining SMs, so all three stages
+// still run at once; other host memory goes through the copy engines.
+
+constexpr int kCopyInSMs = 24;   // ~64 KB of loads in flight per SM covers the host link's latency
+constexpr int kCopyOutSMs = 16;
+
+// Device address of host memory at `p` when the current device can load and
+// store it directly (page-locked and mapped), else nullptr.
+void *device_view(const void *p) {
+    if (g_host_copy != 0 || (reinterpret_cast<uintptr_t>(p) & 3)) return nullptr;  // copy kernels move 4-byte words
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the error state the failed query left
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer || !a.hostPointer) return nullptr;
+    return static_cast<char *>(a.devicePointer) + (static_cast<const char *>(p) - static_cast<const char *>(a.hostPointer));
+}
+
+// Resets the calling thread's grid cap on scope exit.
+struct GridCap {
+    explicit GridCap(int cap) { t_grid_cap = cap; }
+    ~GridCap() { t_grid_cap = 0; }
+};
 
 struct HostPipe {
     cudaStream_t in = nullptr, comp = nullptr, out = nullptr;
@@ -965,13 +996,36 @@ tsm2_status gemm_host(const char *fn, char op, int elem, int64_t m, int64_t n, i
         if ((st = grow(&P->dB, &P->b_bytes, b_need)) != TSM2_SUCCESS) return st;
     }
 
+    // SM copies where the device can address the host buffers (section
+    // comment above); the product kernels get the SMs the copies leave.
+    DeviceState *dev = nullptr;
+    if ((st = device_state(&dev)) != TSM2_SUCCESS) return st;
+    const void *vA = device_view(hA), *vB = device_view(hB);
+    void *vC = device_view(hC);
+    const int in_sms = vA ? kCopyInSMs : 0;
+    int out_sms = 0;
+    if (vC) {  // scaled to the bytes of C per byte of A, at least 2
+        out_sms = (int)std::min<int64_t>(kCopyOutSMs, std::max<int64_t>(2, (kCopyOutSMs * k + n - 1) / n));
+    }
+    GridCap cap(in_sms + out_sms > 0 ? std::max(dev->sm_count - in_sms - out_sms, 1) : 0);
+    static const char *const kCopyNames[8] = {"A:engine B:engine C:engine", "A:sm B:engine C:engine",
+                                              "A:engine B:sm C:engine",     "A:sm B:sm C:engine",
+                                              "A:engine B:engine C:sm",     "A:sm B:engine C:sm",
+                                              "A:engine B:sm C:sm",         "A:sm B:sm C:sm"};
+    t_last_host_copy = kCopyNames[(vA ? 1 : 0) | (vB ? 2 : 0) | (vC ? 4 : 0)];
+
     // Everything starts after the caller's pending work on `stream`.
     if ((e = cudaEventRecord(P->entry, stream)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
     for (cudaStream_t s : {P->in, P->comp, P->out})
         if ((e = cudaStreamWaitEvent(s, P->entry, 0)) != cudaSuccess) return cuda_error(e, "cudaStreamWaitEvent");
-    e = cudaMemcpy2DAsync(P->dB, (size_t)ldbd * elem, hB, (size_t)ldb * elem, (size_t)n * elem, (size_t)k,
-                          cudaMemcpyHostToDevice, P->in);
-    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy2DAsync(B)");
+    if (vB) {
+        e = sm_copy2d_launch(vB, ldb * elem, P->dB, ldbd * elem, n * elem, k, kCopyInSMs, P->in);
+        if (e != cudaSuccess) return cuda_error(e, "host copy kernel (B)");
+    } else {
+        e = cudaMemcpy2DAsync(P->dB, (size_t)ldbd * elem, hB, (size_t)ldb * elem, (size_t)n * elem, (size_t)k,
+                              cudaMemcpyHostToDevice, P->in);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy2DAsync(B)");
+    }
     if ((e = cudaEventRecord(P->b_ready, P->in)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
     if ((e = cudaStreamWaitEvent(P->comp, P->b_ready, 0)) != cudaSuccess) return cuda_error(e, "cudaStreamWaitEvent");
 
@@ -982,9 +1036,15 @@ tsm2_status gemm_host(const char *fn, char op, int elem, int64_t m, int64_t n, i
         const int64_t rows = (m - i0) < mc ? (m - i0) : mc;
         if (chunk >= 2 && (e = cudaStreamWaitEvent(P->in, P->slot_free[slot], 0)) != cudaSuccess)
             return cuda_error(e, "cudaStreamWaitEvent");
-        e = cudaMemcpy2DAsync(P->dA[slot], (size_t)ldd * elem, static_cast<const char *>(hA) + (size_t)i0 * elem,
-                              (size_t)lda * elem, (size_t)rows * elem, (size_t)n, cudaMemcpyHostToDevice, P->in);
-        if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy2DAsync(A chunk)");
+        if (vA) {
+            e = sm_copy2d_launch(static_cast<const char *>(vA) + (size_t)i0 * elem, lda * elem, P->dA[slot],
+                                 ldd * elem, rows * elem, n, in_sms, P->in);
+            if (e != cudaSuccess) return cuda_error(e, "host copy kernel (A chunk)");
+        } else {
+            e = cudaMemcpy2DAsync(P->dA[slot], (size_t)ldd * elem, static_cast<const char *>(hA) + (size_t)i0 * elem,
+                                  (size_t)lda * elem, (size_t)rows * elem, (size_t)n, cudaMemcpyHostToDevice, P->in);
+            if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy2DAsync(A chunk)");
+        }
         if ((e = cudaEventRecord(P->a_ready[slot], P->in)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
         if ((e = cudaStreamWaitEvent(P->comp, P->a_ready[slot], 0)) != cudaSuccess)
             return cuda_error(e, "cudaStreamWaitEvent");
@@ -994,9 +1054,15 @@ tsm2_status gemm_host(const char *fn, char op, int elem, int64_t m, int64_t n, i
         if ((e = cudaEventRecord(P->c_ready[slot], P->comp)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
         if ((e = cudaStreamWaitEvent(P->out, P->c_ready[slot], 0)) != cudaSuccess)
             return cuda_error(e, "cudaStreamWaitEvent");
-        e = cudaMemcpy2DAsync(static_cast<char *>(hC) + (size_t)i0 * elem, (size_t)ldc * elem, P->dC[slot],
-                              (size_t)ldd * elem, (size_t)rows * elem, (size_t)k, cudaMemcpyDeviceToHost, P->out);
-        if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy2DAsync(C chunk)");
+        if (vC) {
+            e = sm_copy2d_launch(P->dC[slot], ldd * elem, static_cast<char *>(vC) + (size_t)i0 * elem, ldc * elem,
+                                 rows * elem, k, out_sms, P->out);
+            if (e != cudaSuccess) return cuda_error(e, "host copy kernel (C chunk)");
+        } else {
+            e = cudaMemcpy2DAsync(static_cast<char *>(hC) + (size_t)i0 * elem, (size_t)ldc * elem, P->dC[slot],
+                                  (size_t)ldd * elem, (size_t)rows * elem, (size_t)k, cudaMemcpyDeviceToHost, P->out);
+            if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy2DAsync(C chunk)");
+        }
         if ((e = cudaEventRecord(P->slot_free[slot], P->out)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
     }
     // The caller's stream resumes once the last C rows are on the host.
@@ -1036,6 +1102,8 @@ tsm2_status tsm2l_s(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda
 const char *tsm2_get_last_error_string(void) { return t_last_error.c_str(); }
 
 const char *tsm2_last_config(void) { return t_last_config; }
+
+const char *tsm2_last_host_copy(void) { return t_last_host_copy; }
 
 tsm2_status tsm2_get_device_status(void *stream) {
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
@@ -1389,6 +1457,8 @@ void tsm2_set_wait_budget_ns(int64_t ns) { g_wait_ns = ns < 0 ? 0 : ns; }
 void tsm2_set_path(int path) { g_path = path; }
 
 void tsm2_set_grid(int blocks) { g_grid_override = blocks < 0 ? 0 : blocks; }
+
+void tsm2_set_host_copy(int mode) { g_host_copy = mode == 1 ? 1 : 0; }
 
 void tsm2_set_trace(unsigned long long *device_words, int64_t blocks) {
     g_trace = device_words;

@@ -24,7 +24,17 @@ def host_colmajor(a, ld, pinned, fill=np.nan):
     return t, t.data_ptr()
 
 
-def run_host(op, dtype, m, n, k, lda=None, ldb=None, ldc=None, pinned=True, rows=None):
+@pytest.fixture
+def copy_mode(request):
+    """Selects the host copy path (0: SM copy kernels, 1: copy engines) for
+    one test and restores the default afterwards."""
+    import paper_2002_03258_gb300 as pkg
+    pkg.tsm2_set_host_copy(request.param)
+    yield request.param
+    pkg.tsm2_set_host_copy(0)
+
+
+def run_host(op, dtype, m, n, k, lda=None, ldb=None, ldc=None, pinned=True, rows=None, expect_copy=None):
     import paper_2002_03258_gb300 as pkg
     lda, ldb, ldc = lda or m, ldb or n, ldc or m
     full = rows is None
@@ -52,6 +62,8 @@ def run_host(op, dtype, m, n, k, lda=None, ldb=None, ldc=None, pinned=True, rows
     s = torch.cuda.Stream()
     st = fn(m, n, k, pA, lda, pB, ldb, tC.data_ptr(), ldc, s.cuda_stream)
     assert st == 0, pkg.tsm2_get_last_error_string()
+    if expect_copy is not None:
+        assert pkg.tsm2_last_host_copy() == expect_copy
     s.synchronize()
     assert pkg.tsm2_get_device_status(0) == 0
     C = tC.numpy().T  # ldc x k
@@ -61,17 +73,46 @@ def run_host(op, dtype, m, n, k, lda=None, ldb=None, ldc=None, pinned=True, rows
     return C[ridx], A, B
 
 
-@pytest.mark.parametrize("pinned", [True, False])
+SM = "A:sm B:sm C:sm"
+ENGINE = "A:engine B:engine C:engine"
+
+
+@pytest.mark.parametrize("pinned,copy_mode", [(True, 0), (True, 1), (False, 0)], indirect=["copy_mode"])
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 @pytest.mark.parametrize("op,m,n,k", [("r", 1000, 777, 5), ("r", 4099, 2048, 16), ("r", 300, 4100, 20),
                                       ("l", 100003, 16, 16), ("l", 5000, 33, 7)])
-def test_host_entry_single_chunk(op, m, n, k, dtype, pinned):
-    C, A, B = run_host(op, dtype, m, n, k, pinned=pinned)
+def test_host_entry_single_chunk(op, m, n, k, dtype, pinned, copy_mode):
+    # Page-locked buffers take the SM copy kernels unless the copy engines
+    # are selected; pageable ones always take the copy engines.
+    C, A, B = run_host(op, dtype, m, n, k, pinned=pinned, expect_copy=SM if pinned and copy_mode == 0 else ENGINE)
     assert_parity(C, A, B, dtype)
 
 
-def test_host_entry_padded_leading_dimensions():
-    C, A, B = run_host("r", np.float32, 1500, 900, 9, lda=1537, ldb=901, ldc=1503)
+@pytest.mark.parametrize("copy_mode", [0, 1], indirect=True)
+def test_host_entry_padded_leading_dimensions(copy_mode):
+    # Leading dimensions that are not multiples of 16 bytes: the copy kernels'
+    # 4-byte path.
+    C, A, B = run_host("r", np.float32, 1500, 900, 9, lda=1537, ldb=901, ldc=1503,
+                       expect_copy=SM if copy_mode == 0 else ENGINE)
+    assert_parity(C, A, B, np.float32)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("m,lda", [(1001, 1004), (1003, 1004), (5, 8), (1, 4)])
+def test_host_entry_vector_copy_with_tail(m, lda, dtype):
+    # 16-byte aligned columns whose height is not a multiple of 16 bytes: the
+    # copy kernels' 16-byte body plus 4-byte tail, in A, B and C.
+    es = np.dtype(dtype).itemsize
+    lda = lda if es == 4 else (m + 1) // 2 * 2
+    for op, n, k in (("r", 2047, 13), ("l", 31, 31)):
+        C, A, B = run_host(op, dtype, m, n, k, lda=lda, ldb=(n + 3) // 4 * 4 if es == 4 else (n + 1) // 2 * 2,
+                           ldc=lda, expect_copy=SM)
+        assert_parity(C, A, B, dtype)
+
+
+@pytest.mark.parametrize("copy_mode", [1], indirect=True)
+def test_host_copy_mode_selects_copy_engines(copy_mode):
+    C, A, B = run_host("l", np.float32, 70001, 24, 24, expect_copy=ENGINE)
     assert_parity(C, A, B, np.float32)
 
 
