@@ -347,8 +347,10 @@ def run_gpu(args):
     value = job_gbs(world, step_bytes, mean_step_ms)
     case_rows = []
     for i, w in enumerate(work32):
-        ms = statistics.mean(per[s][i] for s in range(args.steps))
+        ts = [per[s][i] for s in range(args.steps)]
+        ms = statistics.mean(ts)
         case_rows.append({"op": "tsm2" + w["op"], "m": w["m"], "n": w["n"], "k": w["k"], "ms": round(ms, 4),
+                          "ms_median": round(statistics.median(ts), 4), "ms_min": round(min(ts), 4),
                           "gbs": round(w["bytes"] / (ms * 1e-3) / 1e9, 1),
                           "frac_hbm": round(w["bytes"] / (ms * 1e-3) / 1e9 / peak_hbm, 3),
                           "frac_nominal": round(w["bytes"] / (ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 3),
