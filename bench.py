@@ -312,7 +312,7 @@ def run_gpu(args):
         pkg.check(pkg.tsm2_get_device_status(sh))
         evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in work]
                for _ in range(steps)]
-        configs = {}
+        case_cfg = {}
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -323,14 +323,14 @@ def run_gpu(args):
                 evs[s][i][0].record(stream)
                 pkg.check(call(w))
                 evs[s][i][1].record(stream)
-                configs[i] = pkg.tsm2_last_config()
+                case_cfg[i] = pkg.tsm2_last_config()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         wall = time.perf_counter() - t_region0
         pkg.check(pkg.tsm2_get_device_status(sh))
         per = [[evs[s][i][0].elapsed_time(evs[s][i][1]) for i in range(len(work))] for s in range(steps)]
-        return per, configs, wall
+        return per, case_cfg, wall
 
     peak_hbm, peak_kind = measured_peaks()
     clocks = ClockSampler(local)
@@ -339,7 +339,7 @@ def run_gpu(args):
     work32, bufs32 = make_sweep(4, 0)
     torch.cuda.synchronize()
     clocks.start()
-    per, configs, wall = timed_steps(work32, args.steps, args.warmup)
+    per, case_cfg, wall = timed_steps(work32, args.steps, args.warmup)
     clock_rec = clocks.stop()
     step_ms = [sum(row) for row in per]
     mean_step_ms = ranks_max(statistics.mean(step_ms), dev, world)
@@ -355,16 +355,16 @@ def run_gpu(args):
                           "frac_hbm": round(w["bytes"] / (ms * 1e-3) / 1e9 / peak_hbm, 3),
                           "frac_nominal": round(w["bytes"] / (ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 3),
                           "gflops": round(w["flops"] / (ms * 1e-3) / 1e9, 1),
-                          "config": configs.get(i)})
+                          "config": case_cfg.get(i)})
     dom = max(range(len(work32)), key=lambda i: case_rows[i]["ms"])
     dw = work32[dom]
     dom_ms = case_rows[dom]["ms"]
     achieved = dw["bytes"] / (dom_ms * 1e-3) / 1e9
     wkey = f"{dw['op']}_{dw['m']}x{dw['n']}x{dw['k']}_f32"
-    traffic = traffic_record(configs.get(dom), wkey)
+    traffic = traffic_record(case_cfg.get(dom), wkey)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak_hbm, "unit": "GB/s",
                 "frac": round(achieved / peak_hbm, 4), "traffic": traffic,
-                "kernel": configs.get(dom), "workload": wkey, "peak_kind": peak_kind,
+                "kernel": case_cfg.get(dom), "workload": wkey, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": dw["bytes"]}
 
     # ---- end to end through the C ABI with host buffers --------------------------------------
@@ -440,7 +440,7 @@ def run_gpu(args):
     fp64 = None
     if not args.no_fp64:
         work64, bufs64 = make_sweep(8, 0)
-        per64, configs64, _ = timed_steps(work64, max(1, min(args.steps, 3)), min(args.warmup, 3))
+        per64, case_cfg64, _ = timed_steps(work64, max(1, min(args.steps, 3)), min(args.warmup, 3))
         ms64 = statistics.mean(sum(r) for r in per64)
         bytes64 = sum(w["bytes"] for w in work64)
         flops64 = sum(w["flops"] for w in work64)
@@ -451,7 +451,7 @@ def run_gpu(args):
                 "tflops": round(flops64 / (ms64 * 1e-3) / 1e12, 3),
                 "roofline": {"bound": "alu", "achieved": round(tfl, 3), "peak": FP64_NOMINAL_TFLOPS,
                              "unit": "TFLOP/s", "frac": round(tfl / FP64_NOMINAL_TFLOPS, 4),
-                             "kernel": configs64.get(d64), "peak_kind": "nominal FP64 (recipe)",
+                             "kernel": case_cfg64.get(d64), "peak_kind": "nominal FP64 (recipe)",
                              "workload": f"{work64[d64]['op']}_{work64[d64]['m']}x{work64[d64]['n']}x{work64[d64]['k']}_f64"},
                 "cases": [{"op": "tsm2" + w["op"], "m": w["m"], "n": w["n"], "k": w["k"],
                            "ms": round(statistics.mean(r[i] for r in per64), 4),
