@@ -142,26 +142,36 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax = max(smax, float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
+        with open(self.path) as f:
+            rec = parse_clock_samples(f)
         os.unlink(self.path)
-        if not sm:
-            return None
-        loaded = [x for x in sm if x > 0.5 * smax] or sm
-        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return rec
+
+
+def parse_clock_samples(lines):
+    """Summary of `nvidia-smi --query-gpu=<ClockSampler.FIELDS> --format=csv,
+    noheader,nounits` lines: median SM clock over the samples above half the
+    maximum (the loaded ones), the maximum, and the throttle reasons seen
+    active in any sample.  None without a valid sample."""
+    sm, smax, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            smax = max(smax, float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return None
+    loaded = [x for x in sm if x > 0.5 * smax] or sm
+    return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": sorted(reasons),
+            "samples": len(sm)}
 
 
 def dist_setup():
