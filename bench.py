@@ -793,6 +793,51 @@ def run_case(args):
     return 0
 
 
+def run_host_case(args):
+    """One host-operand multiply (tsm2r_s_host / tsm2l_s_host, binary32): A,
+    B and C in page-locked host memory, the copies inside the timed region
+    (for profiling the host pipeline and its copy kernels).  `mode` 0 moves
+    the buffers with the SM copy kernels, 1 with the copy engines."""
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2002_03258_gb300 as pkg
+    import tsm2_inputs as ti
+    op, m, n, k, mode = args.host_case.split(":")
+    m, n, k, mode = int(m), int(n), int(k), int(mode)
+    if op not in ("r", "l"):
+        raise SystemExit("op must be r or l")
+    lib = pkg.lib()
+    dA = torch.empty((n, m), dtype=torch.float32, device="cuda")
+    pkg.check(lib.tsm2_fill_uniform_s(m, n, 0, ti.MID_A, dA.data_ptr(), m, 0))
+    hA = torch.empty((n, m), dtype=torch.float32, pin_memory=True)
+    hA.copy_(dA)
+    del dA
+    hB = torch.empty((k, n), dtype=torch.float32, pin_memory=True).uniform_(-1, 1)
+    hC = torch.empty((k, m), dtype=torch.float32, pin_memory=True)
+    fn = pkg.tsm2r_s_host if op == "r" else pkg.tsm2l_s_host
+    pkg.tsm2_set_host_copy(mode)
+    ts = []
+    for r in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pkg.check(fn(m, n, k, hA.data_ptr(), m, hB.data_ptr(), n, hC.data_ptr(), m, 0))
+        e1.record()
+        torch.cuda.synchronize()
+        if r >= args.warmup:
+            ts.append(e0.elapsed_time(e1))
+    pkg.check(pkg.tsm2_get_device_status(0))
+    path = pkg.tsm2_last_host_copy()
+    pkg.tsm2_set_host_copy(0)
+    ms = statistics.median(ts)
+    print(json.dumps({"host_case": args.host_case, "config": pkg.tsm2_last_config(), "host_copy": path,
+                      "ms": round(ms, 3), "gbs": round(alg_bytes(m, n, k, 4) / (ms * 1e-3) / 1e9, 1),
+                      "h2d_gbs": round(4 * (m * n + n * k) / (ms * 1e-3) / 1e9, 1),
+                      "d2h_gbs": round(4 * m * k / (ms * 1e-3) / 1e9, 1), "src_hash": src_hash()}), flush=True)
+    return 0
+
+
 def run_batch_case(args):
     """One tile class of the batched workload: the first `count` problems of
     the 512-problem batch whose op is `op` and whose k chunk uses the C-column
@@ -861,9 +906,13 @@ def main():
                          "f32, f64, or for op r bf16 / bf16hilo)")
     ap.add_argument("--batch-case", default=None, help="op:kc:count:flags, e.g. l:32:20:1 -- time one tile class of the "
                     "batched workload (its first `count` problems) as one plan")
+    ap.add_argument("--host-case", default=None, help="op:m:n:k:mode, e.g. r:30720:30720:16:0 -- time one host-operand "
+                    "multiply (binary32; mode 0 SM copy kernels, 1 copy engines)")
     args = ap.parse_args()
     if args.case:
         return run_case(args)
+    if args.host_case:
+        return run_host_case(args)
     if args.batch_case:
         return run_batch_case(args)
     if args.impl == "reference":
