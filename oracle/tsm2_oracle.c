@@ -29,7 +29,11 @@
  * inputs, identity and permutation A (C = P B exactly), all-ones A (every row
  * equal to the column sums of B, bitwise equal across rows), small-integer
  * inputs (exact; compared with integer arithmetic), rank-one A, and the
- * long-double variant below.
+ * long-double variant below.  The magnitude matrix S = |A||B| is pinned for
+ * binary64 and binary32 inputs alike: exact integer arithmetic on signed
+ * small integers (a dropped fabs on either operand fails) and the exact
+ * rational sum of |a||b| on uniform binary32 inputs (a widening through a
+ * narrower type fails).
  */
 #include <stdint.h>
 #include <stddef.h>

@@ -234,3 +234,52 @@ def test_input_distributions_and_random_access():
     assert e.min() == -10 and e.max() == 9
     f32 = ti.uniform_pm1(0, ti.MID_A, 300, 200, np.float32)
     assert np.array_equal(f32, A.astype(np.float32))
+
+
+def test_absgemm_s_exact_on_float32_integers():
+    """Binary32 magnitude matrix S = |A||B| (Sec. 2.1 definition on absolute
+    values) equals integer arithmetic exactly; negative entries in both
+    operands make a dropped fabs on either side fail."""
+    A = ti.int_small(6, ti.MID_A, 33, 47, np.float32)
+    B = ti.int_small(6, ti.MID_B, 47, 5, np.float32)
+    assert (A < 0).any() and (B < 0).any()
+    S = oracle.absgemm(A, B)
+    Si = np.abs(A).astype(np.int64) @ np.abs(B).astype(np.int64)
+    assert S.dtype == np.float64
+    assert np.array_equal(S, Si.astype(np.float64))
+    # a signed product differs from S wherever the signs mix
+    assert not np.array_equal(S, (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64))
+
+
+@pytest.mark.parametrize("m,n,k", [(3, 5, 2), (4, 11, 3), (2, 17, 4)])
+def test_absgemm_s_matches_exact_rational(m, n, k):
+    """S for binary32 uniform inputs: every binary32 value widens exactly to
+    binary64 and all terms are non-negative, so the binary64 sum is within
+    gamma_n(2^-53) * S of the exact rational sum of |a||b|.  A widening that
+    rounded through a narrower type (an error of about 2^-24 per term) or a
+    lost term fails this."""
+    A = ti.uniform_pm1(13, ti.MID_A, m, n, np.float32)
+    B = ti.uniform_pm1(13, ti.MID_B, n, k, np.float32)
+    S = oracle.absgemm(A, B)
+    _, Se = exact_product(A, B)
+    g = oracle.gamma(n, oracle.U_FP64)
+    for i in range(m):
+        for c in range(k):
+            err = abs(Fraction(float(S[i, c])) - Se[i][c])
+            assert err <= Fraction(g) * Se[i][c], (i, c, float(err))
+            # much tighter than one binary32 ulp of S: the widening is exact
+            assert float(err) < 2.0 ** -40 * float(Se[i][c])
+
+
+def test_absgemm_s_strided_and_transposed():
+    """Padded leading dimensions are not read and a transposed view (A^T
+    with row stride lda) gives the transposed magnitude matrix."""
+    m, n, k = 9, 14, 3
+    A = ti.int_small(2, ti.MID_A, m, n, np.float32)
+    B = ti.int_small(2, ti.MID_B, n, k, np.float32)
+    Abuf = ti.padded(A, 12, np.nan)
+    S1 = oracle.absgemm(A, B)
+    S2 = oracle.absgemm(Abuf[:m], B)
+    assert np.array_equal(S1, S2)
+    S3 = oracle.absgemm(B.T, A.T)
+    assert np.array_equal(S3.T, S1)
