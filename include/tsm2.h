@@ -134,10 +134,19 @@ tsm2_status tsm2_rankk_s(int64_t m, int64_t n, int64_t k, const float *dC, int64
  * bytes of binary32 (or the same bytes, with about 16 significant bits, for
  * hi + lo), and the products run on the tensor cores (B is split internally
  * into bfloat16 pieces b1 + b2 + b3 = b exactly; plain A uses b1 + b2, B to
- * about 16 bits, hi + lo all three).  Error: |C - A_hi B| <= about
- * (2^-18 + 2 n 2^-23) |A_hi||B| (plain), |C - (A_hi + A_lo) B| <= about
- * (2^-27 + 5 n 2^-23) |A||B| (hi + lo).  The bulk-copy path needs 16-byte
- * aligned A_hi/A_lo and lda a multiple of 8; otherwise an element-wise
+ * 17 bits, hi + lo all three).  Error, componentwise against the product of
+ * the bfloat16-represented A (A_eff = A_hi or A_hi + A_lo), with S = |A_eff||B|,
+ * G inner indices summed on the tensor cores per drain (256 plain, 32 hi + lo)
+ * in s = 16 (plain) or 4 (hi + lo) MMA steps, and P the stream-K partial sums
+ * that cover one row block (at most ceil((U - 1) / u) + 1 for U pipeline stages
+ * per row block and u >= 4 stages per thread block at the default grid; 4 at
+ * 32768 x 32768):
+ *   |C - A_eff B| <= 1.04 (e_B + 18 s 2^-23 + gamma_{NP-1} + gamma_{n/G + P}) S,
+ * e_B = 2^-17 (plain) or 0 (hi + lo), NP = 2 or 3 pieces, gamma_j = j 2^-24 /
+ * (1 - j 2^-24); the tensor-core term assumes the aligned, truncating sums
+ * measured on earlier NVIDIA tensor cores.  About 5e-5 S (plain) and 7e-5 S
+ * (hi + lo) at n = 32768.  The element-wise path: gamma_n S.  The bulk-copy
+ * path needs 16-byte aligned A_hi/A_lo and lda a multiple of 8; otherwise an element-wise
  * CUDA-core path runs.  Uses the workspace (B pieces and split partial sums).
  * Same error contract as tsm2r_s. */
 tsm2_status tsm2r_bf16(int64_t m, int64_t n, int64_t k, const uint16_t *A_hi, const uint16_t *A_lo,
