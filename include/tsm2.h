@@ -88,8 +88,13 @@ tsm2_status tsm2r_s(int64_t m, int64_t n, int64_t k,
                     float *C, int64_t ldc, void *stream);
 
 /* TSM2L, binary64 (Sec. 3.2, Algorithm 5: a persistent grid of thread
- * blocks strides over row blocks of the tall-and-skinny A; B is held on
- * chip).  TSM2_ERR_UNSUPPORTED if n > 64 or k > 64. */
+ * blocks strides over row blocks of the tall-and-skinny A).  Any n, k >= 0.
+ * For n <= 64 B is held on chip for the whole call; for n > 64 B is staged
+ * through shared memory beside each stage of A (the staged-B setting of
+ * Algorithm 6, Sec. 3.2.2).  C is produced in groups of up to 32 columns, A
+ * read once per group (ceil(k/32) times).  Same pointer, stream, alignment,
+ * accuracy and error contract as tsm2r_d; TSM2_ERR_UNSUPPORTED is not
+ * returned for any n or k. */
 tsm2_status tsm2l_d(int64_t m, int64_t n, int64_t k,
                     const double *A, int64_t lda,
                     const double *B, int64_t ldb,
@@ -266,7 +271,9 @@ typedef struct tsm2_batch_plan_s *tsm2_batch_plan_t;
 
 /* Validates the problems (argument rules of tsm2r_s; additionally every A,
  * and B of TSM2R problems, must be 16-byte aligned with 16-byte multiple
- * leading-dimension strides: TSM2_ERR_UNSUPPORTED otherwise), encodes their
+ * leading-dimension strides, and TSM2L problems need n <= 64 and k <= 64
+ * because batched TSM2L classes hold B on chip: TSM2_ERR_UNSUPPORTED
+ * otherwise; the single-problem tsm2l_s has no such limit), encodes their
  * tensor maps and uploads the plan's tables and workspace (cudaMalloc: make
  * plans outside timed or captured regions).  The operand pointers are
  * recorded: the plan computes on whatever those buffers hold at execution.
