@@ -76,9 +76,9 @@ def launches_per_call(op, n, k):
     return total
 
 
-# Sources that define and launch the bulk-copy kernels (the dominant kernel's
+# Device sources of the bulk-copy kernels (the dominant kernel's
 # DRAM-traffic record is tied to these).
-KERNEL_SOURCES = ("common.cuh", "internal.h", "tsm2_api.cu", "tsm2_cfg.cuh", "tsm2_stream.cu")
+KERNEL_SOURCES = ("common.cuh", "internal.h", "tsm2_cfg.cuh", "tsm2_stream.cu")
 
 
 def src_hash():
@@ -202,6 +202,47 @@ def job_gbs(world, step_bytes, ms):
 # ---------------------------------------------------------------------------
 # CPU oracle arm (reference arm and cpu_baseline)
 
+def measure_fma_peak(elem, target_ms=20.0, reps=5):
+    """FMA throughput of this GPU from the library's probe kernel
+    (tsm2_fma_probe): 8 blocks of 256 threads per SM, independent chains,
+    sized to run about `target_ms` (as long as the FP64 kernels it is
+    compared with, so both see the clocks of a loaded GPU).  Best of `reps`
+    CUDA-event timings after one warm-up."""
+    import torch
+
+    import paper_2002_03258_gb300 as pkg
+    lib = pkg.lib()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks = 8 * sms
+    threads = blocks * 256
+    per_iter = 16 if elem == 8 else 32  # flops per thread per step
+    guess = 1.25e12 if elem == 8 else 80e12
+    iters = max(100, int(guess * target_ms * 1e-3 / (per_iter * threads)))
+    sink = torch.empty(threads, dtype=torch.float64 if elem == 8 else torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    best = float("inf")
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pkg.check(lib.tsm2_fma_probe(elem, blocks, iters, sink.data_ptr(), stream.cuda_stream))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r > 0:
+            best = min(best, e0.elapsed_time(e1))
+    flops = float(per_iter) * iters * threads
+    return {"tflops": round(flops / (best * 1e-3) / 1e12, 4), "ms": round(best, 3), "blocks": blocks,
+            "iters": iters, "kind": "DFMA chains" if elem == 8 else "FFMA2 chains"}
+
+
+def host_cores():
+    """Cores this process may run on (its CPU affinity set), not every core
+    of the host."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def oracle_sample_run(dtype_name, steps, warmup, budget_s=20.0):
     """Time the CPU oracle on a bounded row sample of every case of the sweep.
 
@@ -212,7 +253,7 @@ def oracle_sample_run(dtype_name, steps, warmup, budget_s=20.0):
     import tsm2_inputs as ti
     dt = np.float32 if dtype_name == "f32" else np.float64
     es = 4 if dt == np.float32 else 8
-    cores = os.cpu_count() or 1
+    cores = host_cores()
     samples = []
     for op, m, n, k, _ in cases(es):
         rows = max(64, min(m, (1 << 21) // n))  # about 2M elements of A per case
@@ -246,8 +287,9 @@ def run_reference(args):
         "impl": "reference", "metric": "TSM2R/TSM2L achieved HBM GB/s (binary32 sweep)", "value": round(value, 4),
         "unit": "GB/s", "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
         "ms_per_step": round(t * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD + " (row sample, CPU)", "sample": desc},
+        "dtype": "f32", "accumulate": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (row sample, CPU)", "sample": desc,
+                   "arithmetic": "binary32 inputs widened exactly, products and sums in binary64"},
         "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -449,6 +491,7 @@ def run_gpu(args):
     # ---- binary64 sweep (FP64 ALU bound) ----------------------------------------------------
     fp64 = None
     if not args.no_fp64:
+        fma64 = measure_fma_peak(8)
         work64, bufs64 = make_sweep(8, 0)
         per64, case_cfg64, _ = timed_steps(work64, max(1, min(args.steps, 3)), min(args.warmup, 3))
         ms64 = statistics.mean(sum(r) for r in per64)
@@ -459,9 +502,11 @@ def run_gpu(args):
         tfl = work64[d64]["flops"] / (d64_ms * 1e-3) / 1e12
         fp64 = {"value": round(bytes64 / (ms64 * 1e-3) / 1e9, 1), "unit": "GB/s", "ms_per_step": round(ms64, 3),
                 "tflops": round(flops64 / (ms64 * 1e-3) / 1e12, 3),
-                "roofline": {"bound": "alu", "achieved": round(tfl, 3), "peak": FP64_NOMINAL_TFLOPS,
-                             "unit": "TFLOP/s", "frac": round(tfl / FP64_NOMINAL_TFLOPS, 4),
-                             "kernel": case_cfg64.get(d64), "peak_kind": "nominal FP64 (recipe)",
+                "roofline": {"bound": "alu", "achieved": round(tfl, 3), "peak": fma64["tflops"],
+                             "unit": "TFLOP/s", "frac": round(tfl / fma64["tflops"], 4),
+                             "kernel": case_cfg64.get(d64), "peak_kind": "measured (DFMA probe, this run)",
+                             "peak_probe": fma64, "nominal_peak": FP64_NOMINAL_TFLOPS,
+                             "frac_nominal": round(tfl / FP64_NOMINAL_TFLOPS, 4),
                              "workload": f"{work64[d64]['op']}_{work64[d64]['m']}x{work64[d64]['n']}x{work64[d64]['k']}_f64"},
                 "cases": [{"op": "tsm2" + w["op"], "m": w["m"], "n": w["n"], "k": w["k"],
                            "ms": round(statistics.mean(r[i] for r in per64), 4),

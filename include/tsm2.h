@@ -55,6 +55,11 @@
  *    that the library allocates lazily with cudaMalloc on first use and
  *    grows when needed; tsm2_shutdown() frees it.  Two calls in flight at
  *    once on the SAME stream are ordered by the stream and never race.
+ *    Growing synchronises the stream and calls cudaMalloc, which cannot
+ *    happen while the stream is captured into a CUDA graph: a call that
+ *    would grow the workspace during capture returns TSM2_ERR_UNSUPPORTED
+ *    (the capture itself stays valid).  Call the largest shape once on the
+ *    stream before capturing.
  */
 #ifndef TSM2_H
 #define TSM2_H
@@ -217,15 +222,20 @@ tsm2_status tsm2l_d_host(int64_t m, int64_t n, int64_t k, const double *A, int64
  * pool that has reserved the free memory), or a latency-bound loop that
  * cannot pay for cudaMalloc and its implicit synchronisation.
  *  - Scratch: partial sums of row blocks split between thread blocks, their
- *    arrival counters and (column chunks 9..16 wide) a packed n x 16 copy of
- *    B live in a fixed 16 MiB array in device memory that every GPU loading
- *    the library holds until the process exits.  No call of this function
- *    allocates or frees device memory.
+ *    arrival counters and (column chunks 9..16 wide, KC = 12 or 16 columns)
+ *    a packed n x KC copy of B live in a fixed 16 MiB array in device memory.
+ *    The array belongs to the library's device code: it is reserved, with the
+ *    library's status word, when that code is first loaded on a device, which
+ *    is the first call of any tsm2 entry point there (CUDA loads modules
+ *    lazily), and it stays reserved until the process exits.  No call of this
+ *    function allocates or frees device memory after that.  A caller whose
+ *    allocator reserves all free device memory should make one tsm2 call on
+ *    each device first, or that first call can fail for lack of memory.
  *  - Limit: those must fit the array: m up to about 222,000 rows when a
- *    column chunk is 9..16 wide and n is small, fewer as n grows (64 bytes of
- *    packed B per inner index), more for narrower k (the sizes are in the
- *    error message).  Larger problems return TSM2_ERR_UNSUPPORTED before
- *    anything is launched.
+ *    column chunk is 9..16 wide and n is small, fewer as n grows (4 KC bytes
+ *    of packed B per inner index: 48 for KC = 12, 64 for KC = 16), more for
+ *    narrower k (the sizes are in the error message).  Larger problems return
+ *    TSM2_ERR_UNSUPPORTED before anything is launched.
  *  - Set-up: the first call on each device looks up the array's device
  *    address (cudaGetSymbolAddress) with that device current; make that first
  *    call before any stream capture.
@@ -379,6 +389,17 @@ tsm2_status tsm2_fill_normal_ih_s(int64_t rows, int64_t cols, uint64_t seed, uin
                                   double scale, float *X, int64_t ldx, void *stream);
 tsm2_status tsm2_fill_logmag_s(int64_t rows, int64_t cols, uint64_t seed, uint64_t matrix_id,
                                float *X, int64_t ldx, void *stream);
+
+/* FMA throughput probe for the roofline denominators (not part of the
+ * multiply; the paper's model takes the peak FMA rate as an input, Sec. 3.1.8).
+ * Launches `blocks` blocks of 256 threads, each thread running 8 independent
+ * multiply-add chains of `iters` steps in binary64 (elem = 8, DFMA) or packed
+ * binary32 (elem = 4, FFMA2, two lanes per instruction), and writes one value
+ * per thread to `sink` (device, blocks * 256 elements of the element type).
+ * Work: 16 * iters flops per thread (elem 8) or 32 * iters (elem 4).  The
+ * caller times it.  TSM2_ERR_INVALID_VALUE for a bad elem, blocks < 1,
+ * iters < 0 or a NULL sink. */
+tsm2_status tsm2_fma_probe(int elem, int blocks, int64_t iters, void *sink, void *stream);
 
 #ifdef __cplusplus
 }

@@ -48,12 +48,9 @@ def _load():
             lib = ctypes.CDLL(LIB_PATH)
             i64, vp, u64 = ctypes.c_int64, ctypes.c_void_p, ctypes.c_uint64
             gemm_sig = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]
-            for name in ("tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s", "tsm2r_s_noalloc",
-                         "tsm2r_s_host", "tsm2r_d_host", "tsm2l_s_host", "tsm2l_d_host", "tsm2x_s", "tsm2x_d", "tsm2x_choice", "tsm2x_s", "tsm2x_d"):
-                f = getattr(lib, name)
-                f.argtypes = gemm_sig
-                f.restype = ctypes.c_int
-            for name in ("tsm2r_t_d", "tsm2r_t_s", "tsm2_rankk_d", "tsm2_rankk_s"):
+            for name in ("tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s", "tsm2x_d", "tsm2x_s", "tsm2r_s_noalloc",
+                         "tsm2r_s_host", "tsm2r_d_host", "tsm2l_s_host", "tsm2l_d_host",
+                         "tsm2r_t_d", "tsm2r_t_s", "tsm2_rankk_d", "tsm2_rankk_s"):
                 f = getattr(lib, name)
                 f.argtypes = gemm_sig
                 f.restype = ctypes.c_int
@@ -102,6 +99,8 @@ def _load():
                 f = getattr(lib, name)
                 f.argtypes = [i64, i64, u64, u64, vp, i64, vp]
                 f.restype = ctypes.c_int
+            lib.tsm2_fma_probe.argtypes = [ctypes.c_int, ctypes.c_int, i64, vp, vp]
+            lib.tsm2_fma_probe.restype = ctypes.c_int
             for name in ("tsm2_fill_normal_ih_d", "tsm2_fill_normal_ih_s"):
                 f = getattr(lib, name)
                 f.argtypes = [i64, i64, u64, u64, ctypes.c_double, vp, i64, vp]

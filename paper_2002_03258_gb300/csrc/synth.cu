@@ -80,9 +80,56 @@ tsm2_status fill(int64_t rows, int64_t cols, uint64_t seed, uint64_t mid, int di
     return cudaGetLastError() == cudaSuccess ? TSM2_SUCCESS : TSM2_ERR_CUDA;
 }
 
+// FMA throughput probe: every thread runs kChains independent multiply-add
+// chains for `iters` steps (x <- x * a + c, no chain waits on another), so
+// the FMA pipes, not latency, set the rate.  The values stay bounded (|a| < 1)
+// and the chains' sum goes to `sink` so nothing is optimised away.
+constexpr int kChains = 8;
+
+__global__ void __launch_bounds__(256) fma_probe_f64(int64_t iters, double *sink) {
+    double x[kChains];
+    const double a = 0.999999 - 1e-9 * (threadIdx.x & 7), c = 1e-7 * (1 + (blockIdx.x & 3));
+#pragma unroll
+    for (int q = 0; q < kChains; ++q) x[q] = 0.5 + 0.01 * q + 1e-6 * threadIdx.x;
+    for (int64_t it = 0; it < iters; ++it)
+#pragma unroll
+        for (int q = 0; q < kChains; ++q) x[q] = fma(x[q], a, c);
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < kChains; ++q) s += x[q];
+    sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// binary32 with packed FFMA2 (two lanes per instruction), as the kernels use.
+__global__ void __launch_bounds__(256) fma_probe_f32(int64_t iters, float *sink) {
+    float2 x[kChains];
+    const float a = 0.9999f - 1e-6f * (threadIdx.x & 7), c = 1e-5f * (1 + (blockIdx.x & 3));
+    const float2 aa = make_float2(a, a), cc = make_float2(c, c);
+#pragma unroll
+    for (int q = 0; q < kChains; ++q) x[q] = make_float2(0.5f + 0.01f * q, 0.25f + 1e-4f * threadIdx.x);
+    for (int64_t it = 0; it < iters; ++it)
+#pragma unroll
+        for (int q = 0; q < kChains; ++q) x[q] = __ffma2_rn(x[q], aa, cc);
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < kChains; ++q) s += x[q].x + x[q].y;
+    sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
 
 extern "C" {
+
+tsm2_status tsm2_fma_probe(int elem, int blocks, int64_t iters, void *sink, void *stream) {
+    if ((elem != 4 && elem != 8) || blocks < 1 || iters < 0 || !sink)
+        return TSM2_ERR_INVALID_VALUE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (elem == 8)
+        fma_probe_f64<<<blocks, 256, 0, st>>>(iters, static_cast<double *>(sink));
+    else
+        fma_probe_f32<<<blocks, 256, 0, st>>>(iters, static_cast<float *>(sink));
+    return cudaGetLastError() == cudaSuccess ? TSM2_SUCCESS : TSM2_ERR_CUDA;
+}
 
 tsm2_status tsm2_fill_uniform_d(int64_t rows, int64_t cols, uint64_t seed, uint64_t mid, double *X, int64_t ldx,
                                 void *stream) {

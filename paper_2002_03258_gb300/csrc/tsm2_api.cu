@@ -97,6 +97,15 @@ tsm2_status workspace(cudaStream_t stream, size_t counter_bytes, size_t slot_byt
     std::lock_guard<std::mutex> lk(g_mu);
     Workspace &w = g_ws[{dev, reinterpret_cast<uintptr_t>(stream)}];
     if (!w.ptr || w.counter_bytes < counter_bytes || w.bytes < w.counter_bytes + slot_bytes) {
+        // Growing needs a synchronize and cudaMalloc, neither of which may
+        // run while the stream is being captured into a graph.
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(stream, &cap);
+        if (e != cudaSuccess) return cuda_error(e, "cudaStreamIsCapturing");
+        if (cap != cudaStreamCaptureStatusNone)
+            return set_error(TSM2_ERR_UNSUPPORTED,
+                             "the stream's workspace must grow, which cannot happen during stream capture: call the "
+                             "largest shape once on this stream before capturing");
         const size_t cb = std::max(counter_bytes, w.counter_bytes);
         const size_t nb = std::max((cb + slot_bytes) * 5 / 4 + 4096, w.bytes);
         if (w.ptr) {

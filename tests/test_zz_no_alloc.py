@@ -57,3 +57,31 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     st = lib.tsm2r_s_noalloc(m, n, k, fake, m, fake + (1 << 32), n, fake + (1 << 34), m, 0)
     assert st == pkg.ERR_UNSUPPORTED
     assert "static scratch" in pkg.tsm2_get_last_error_string()
+
+
+def test_noalloc_allocates_no_device_memory():
+    """The defining property: after one warm-up call has loaded the library's
+    device code, calls on a stream the library has never seen (tsm2r_s would
+    allocate a workspace for it) leave the device's free memory unchanged."""
+    import paper_2002_03258_gb300 as pkg
+    pkg.tsm2_set_path(0)
+    pkg.tsm2_set_grid(0)
+    lib = pkg.lib()
+    m, n, k = 10240, 10240, 16  # row blocks split between thread blocks: scratch needed
+    A = ti.uniform_pm1(2, ti.MID_A, m, n, np.float32)
+    B = ti.uniform_pm1(2, ti.MID_B, n, k, np.float32)
+    dA, dB = DevMat(A), DevMat(B)
+    out = DevMat(np.zeros((m, k), np.float32))
+    assert lib.tsm2r_s_noalloc(m, n, k, dA.ptr, m, dB.ptr, n, out.ptr, m, 0) == 0
+    torch.cuda.synchronize()
+    fresh = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        st = lib.tsm2r_s_noalloc(m, n, k, dA.ptr, m, dB.ptr, n, out.ptr, m, fresh.cuda_stream)
+        assert st == 0, pkg.tsm2_get_last_error_string()
+    fresh.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0, (free0, free1)
+    assert pkg.tsm2_get_device_status(0) == 0
+    assert_parity(out.numpy(), A, B, np.float32)
