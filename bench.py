@@ -42,6 +42,7 @@ L_MS = [2 ** 20, 2 ** 23]
 L_NS = [8, 16, 32]
 WORKLOAD = ("tsm2 sweep: TSM2R n x n * n x k, n in {10240,20480,30720}, k in {2,4,8,16}; "
             "TSM2L m x n * n x n, m in {2^20,2^23}, n in {8,16,32}; uniform[-1,1) seed 0")
+BATCH_PITCH_BYTES = 512     # batched workload: leading dimensions rounded up to 512 bytes (pitched allocation)
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 nominal FP64 (no FP64 tensor-core speed-up)
 NOMINAL_HBM_GBS = 8000.0     # GB300 HBM3e, nominal (~8 TB/s)
 FALLBACK_HBM_GBS = 6800.0
@@ -64,16 +65,10 @@ def alg_bytes(m, n, k, es):
 
 def launches_per_call(op, n, k):
     """Kernels one tsm2r_s / tsm2l_s call launches (binary32, bulk-copy path):
-    one per column chunk (16 for TSM2R, 32 for TSM2L), plus the B packing
-    kernel before each chunk that reads B row-major (TSM2R chunks of 9..16
-    columns; staged-B TSM2L, n > 64)."""
+    one per column chunk (16 columns for TSM2R, 32 for TSM2L).  B reaches the
+    kernels as it is (row-major configurations transpose it on chip)."""
     kc = 32 if op == "l" else 16
-    total = 0
-    for c0 in range(0, k, kc):
-        kk = min(kc, k - c0)
-        packs = (op == "r" and kk > 8) or (op == "l" and n > 64)
-        total += 1 + int(packs)
-    return total
+    return -(-k // kc) if k > 0 else 0
 
 
 # Device sources of the bulk-copy kernels (the dominant kernel's
@@ -626,32 +621,33 @@ def run_gpu(args):
         del X, Bm, hi, lo, Cm
         torch.cuda.empty_cache()
 
-    # ---- batched uneven problems: one graph launch vs a loop of plain launches ---------------
+    # ---- batched uneven problems: one persistent launch vs a loop of plain launches ----------
     batched = None
     if not args.no_batched:
         import paper_2002_03258_gb300.batched as bt
-        from paper_2002_03258_gb300.autotune import autotune
+        from paper_2002_03258_gb300.autotune import autotune, make_plan
         shapes = ti.batch_shapes(0)
-        probs, keep, loop_calls = [], [], []
-        total = 0
-        for idx, (op, m, n, k) in enumerate(shapes):
-            lda = (m + 3) // 4 * 4
-            ldb = (n + 3) // 4 * 4
-            tA = torch.empty((n, lda), dtype=torch.float32, device=dev)
-            tB = torch.empty((k, ldb), dtype=torch.float32, device=dev)
-            tC = torch.empty((k, lda), dtype=torch.float32, device=dev)
-            pkg.check(lib.tsm2_fill_uniform_s(m, n, idx, ti.MID_A, tA.data_ptr(), lda, sh))
-            pkg.check(lib.tsm2_fill_uniform_s(n, k, idx, ti.MID_B, tB.data_ptr(), ldb, sh))
-            keep += [tA, tB, tC]
-            probs.append(bt.problem(op, m, n, k, tA.data_ptr(), lda, tB.data_ptr(), ldb, tC.data_ptr(), lda))
-            fn = pkg.tsm2r_s if op == "r" else pkg.tsm2l_s
-            loop_calls.append((fn, (m, n, k, tA.data_ptr(), lda, tB.data_ptr(), ldb, tC.data_ptr(), lda, sh)))
-            total += 4 * (m * n + n * k + m * k)
-        torch.cuda.synchronize()
 
-        def loop():
-            for fn, a in loop_calls:
-                pkg.check(fn(*a))
+        def build_batch(pitch_bytes):
+            """Device buffers of the 512 problems, leading dimensions rounded
+            up to `pitch_bytes`; returns (problems, buffers, plain calls, bytes)."""
+            pe = max(1, pitch_bytes // 4)
+            probs_, keep_, calls_, tot = [], [], [], 0
+            for idx, (op, m, n, k) in enumerate(shapes):
+                lda = (m + pe - 1) // pe * pe
+                ldb = (n + pe - 1) // pe * pe
+                tA = torch.empty((n, lda), dtype=torch.float32, device=dev)
+                tB = torch.empty((k, ldb), dtype=torch.float32, device=dev)
+                tC = torch.empty((k, lda), dtype=torch.float32, device=dev)
+                pkg.check(lib.tsm2_fill_uniform_s(m, n, idx, ti.MID_A, tA.data_ptr(), lda, sh))
+                pkg.check(lib.tsm2_fill_uniform_s(n, k, idx, ti.MID_B, tB.data_ptr(), ldb, sh))
+                keep_ += [tA, tB, tC]
+                probs_.append(bt.problem(op, m, n, k, tA.data_ptr(), lda, tB.data_ptr(), ldb, tC.data_ptr(), lda))
+                fn = pkg.tsm2r_s if op == "r" else pkg.tsm2l_s
+                calls_.append((fn, (m, n, k, tA.data_ptr(), lda, tB.data_ptr(), ldb, tC.data_ptr(), lda, sh)))
+                tot += 4 * (m * n + n * k + m * k)
+            torch.cuda.synchronize()
+            return probs_, keep_, calls_, tot
 
         def timed(fn, reps):
             ts = []
@@ -666,36 +662,65 @@ def run_gpu(args):
             return statistics.median(ts)
 
         reps = max(3, min(args.steps, 5))
+        probs, keep, loop_calls, total = build_batch(BATCH_PITCH_BYTES)
+
+        def loop():
+            for fn, a in loop_calls:
+                pkg.check(fn(*a))
+
         loop()
         t_loop = timed(loop, reps)
-        plan0 = bt.BatchPlan(probs, 0)
+        plan0 = make_plan(probs, 0, 0, "single")
         plan0.graph_launch(sh)
         t_default = timed(lambda: plan0.graph_launch(sh), reps)
         classes0 = plan0.classes()
+        launches0 = plan0.num_launches()
         plan0.close()
-        tuned, rec = autotune(probs, reps=3, flush=l2_flush)
+        tuned, rec = autotune(probs, reps=3, flush=l2_flush, hbm_gbs=peak_hbm)
         t_tuned = timed(lambda: tuned.graph_launch(sh), reps)
         pkg.check(pkg.tsm2_get_device_status(sh))
+        best_single = min((t for t in rec["trials"] if t["mode"] == "single"), key=lambda t: t["ms"])
+        best_serial = min((t for t in rec["trials"] if t["mode"] == "serial"), key=lambda t: t["ms"])
         batched = {
             "workload": "512 problems: 256 TSM2R (n = m uniform in [512, 8192], k in {2..16}), 256 TSM2L "
-                        "(m in [2^14, 2^20], n = k in {4..32}), binary32 uniform[-1,1), seed 0",
+                        "(m in [2^14, 2^20], n = k in {4..32}), binary32 uniform[-1,1), seed 0; leading "
+                        f"dimensions rounded up to {BATCH_PITCH_BYTES} bytes",
             "algorithmic_bytes": total,
             "loop_of_plain_launches_ms": round(t_loop, 4),
-            "graph_default_shares_ms": round(t_default, 4),
+            "graph_single_launch_default_ms": round(t_default, 4),
             "graph_autotuned_ms": round(t_tuned, 4),
             "gbs": {"loop": round(total / (t_loop * 1e-3) / 1e9, 1),
-                    "graph_default": round(total / (t_default * 1e-3) / 1e9, 1),
+                    "single_launch_default": round(total / (t_default * 1e-3) / 1e9, 1),
+                    "best_single_launch": round(total / (best_single["ms"] * 1e-3) / 1e9, 1),
+                    "best_serial_classes": round(total / (best_serial["ms"] * 1e-3) / 1e9, 1),
                     "graph_autotuned": round(total / (t_tuned * 1e-3) / 1e9, 1)},
+            "frac_hbm_autotuned": round(total / (t_tuned * 1e-3) / 1e9 / peak_hbm, 3),
             "speedup_autotuned_vs_loop": round(t_loop / t_tuned, 3),
-            "autotuned": {"flags": rec["flags"], "grids": rec["grids"], "serial": rec["serial"],
-                          "classes": [c["name"] for c in tuned.classes()]},
-            "default_classes": [(c["name"], c["nprob"], c["grid"]) for c in classes0],
-            "trials": [(t["flags"], t["shares"], t["ms"]) for t in rec["trials"]],
-            "class_alone_ms": {str(t["flags"]): list(zip(t["classes"], t["class_alone_ms"]))
-                               for t in rec["trials"] if t["shares"] == "bytes"},
+            "launches": {"loop": sum(launches_per_call(o, n, k) for o, m, n, k in shapes),
+                         "single_launch": launches0, "autotuned": tuned.num_launches()},
+            "autotuned": {k2: rec[k2] for k2 in ("variant", "flags", "mode", "launches", "seed", "model")}
+            | {"classes": [c["name"] for c in tuned.classes()],
+               "tile": {k2: v2 for k2, v2 in rec["trials"][[t["variant"] == rec["variant"] and t["flags"] == rec["flags"]
+                                                            and t["mode"] == rec["mode"] for t in rec["trials"]].index(True)].items()
+                        if k2 in ("stages", "rows_per_lane", "inner_per_warp")}},
+            "default_classes": [(c["name"], c["nprob"]) for c in classes0],
+            "trials": [(t["variant"], t["flags"], t["mode"], t["launches"], t["ms"]) for t in rec["trials"]],
+            "trial_fields": ["variant", "flags", "mode", "launches", "ms"],
         }
         tuned.close()
         del keep, probs, loop_calls
+        torch.cuda.empty_cache()
+        # Same batch with leading dimensions only 16-byte aligned: 1 KB column
+        # runs of A then straddle DRAM lines (the tuned choice, re-timed).
+        probs, keep, _, _ = build_batch(16)
+        p16 = make_plan(probs, rec["variant"], rec["flags"], rec["mode"])
+        p16.graph_launch(sh)
+        t16 = timed(lambda: p16.graph_launch(sh), reps)
+        pkg.check(pkg.tsm2_get_device_status(sh))
+        p16.close()
+        batched["pitch16_autotuned_ms"] = round(t16, 4)
+        batched["gbs"]["pitch16_autotuned"] = round(total / (t16 * 1e-3) / 1e9, 1)
+        del keep, probs
         torch.cuda.empty_cache()
 
     # ---- TSM2R / TSM2L crossover and the TSM2X choice -------------------------------------------
@@ -895,15 +920,18 @@ def run_batch_case(args):
     import paper_2002_03258_gb300 as pkg
     import paper_2002_03258_gb300.batched as bt
     import tsm2_inputs as ti
-    op, kc, count, flags = args.batch_case.split(":")
+    parts = args.batch_case.split(":")
+    op, kc, count, flags = parts[:4]
     kc, count, flags = int(kc), int(count), int(flags)
+    pitch = int(parts[4]) if len(parts) > 4 else 16  # bytes: leading dimensions rounded up to this
+    pe = max(1, pitch // 4)
     widths = (2, 4, 8, 12, 16, 24, 32)
     lib = pkg.lib()
     probs, keep, total = [], [], 0
     for idx, (o, m, n, k) in enumerate(ti.batch_shapes(0)):
         if o != op or next(w for w in widths if w >= min(k, 32 if o == "l" else 16)) != kc or len(probs) >= count:
             continue
-        lda, ldb = (m + 3) // 4 * 4, (n + 3) // 4 * 4
+        lda, ldb = (m + pe - 1) // pe * pe, (n + pe - 1) // pe * pe
         tA = torch.empty((n, lda), dtype=torch.float32, device="cuda")
         tB = torch.empty((k, ldb), dtype=torch.float32, device="cuda")
         tC = torch.empty((k, lda), dtype=torch.float32, device="cuda")
@@ -949,7 +977,7 @@ def main():
     ap.add_argument("--no-crossover", action="store_true")
     ap.add_argument("--case", default=None, help="op:dtype:m:n:k, e.g. r:f32:8192:8192:16 -- time one multiply only (op r, l or x; dtype "
                          "f32, f64, or for op r bf16 / bf16hilo)")
-    ap.add_argument("--batch-case", default=None, help="op:kc:count:flags, e.g. l:32:20:1 -- time one tile class of the "
+    ap.add_argument("--batch-case", default=None, help="op:kc:count:flags[:pitch], e.g. l:32:20:1 -- time one tile class of the "
                     "batched workload (its first `count` problems) as one plan")
     ap.add_argument("--host-case", default=None, help="op:m:n:k:mode, e.g. r:30720:30720:16:0 -- time one host-operand "
                     "multiply (binary32; mode 0 SM copy kernels, 1 copy engines)")

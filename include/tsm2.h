@@ -252,14 +252,23 @@ tsm2_status tsm2r_s_noalloc(int64_t m, int64_t n, int64_t k,
 /* ---- Batches of uneven problems (binary32) ----------------------------------
  *
  * Many TSM2R / TSM2L problems of different shapes executed as one unit.  The
- * problems are grouped into tile classes (schedule and C-column width); each
- * class runs as ONE persistent kernel whose blocks each take an equal,
- * contiguous share of the class's work units, crossing problem boundaries
+ * problems are grouped into tile classes (schedule and C-column width KC:
+ * TSM2R with 8 or 16 columns, TSM2L with 8, 16, 24 or 32; each column chunk
+ * goes to the narrowest class that holds it).  In every class the work units
+ * of all its problems are numbered end to end and every block of a persistent
+ * grid takes an equal, contiguous share, crossing problem boundaries
  * (Algorithm 5's persistent walk over tiles, Sec. 3.2.2, extended across
- * problems).  The class kernels run concurrently on SM shares set by
- * tsm2_batch_plan_set_grids (by default proportional to their bytes; the
- * Python autotuner measures and sets them), and a whole batch can be replayed
- * as one CUDA graph launch. */
+ * problems).  The tile parameters that the paper tunes offline (Sec. 3.1.9,
+ * 3.2.2) come in compiled variants (pipeline stages, rows of C per lane,
+ * inner columns per warp and stage), chosen per plan.  Execution modes:
+ *  - TSM2_BATCH_SINGLE_LAUNCH (default): ONE persistent kernel whose blocks
+ *    walk their share of every class in turn, through one pipeline;
+ *  - TSM2_BATCH_SERIAL: one launch per class, each on all SMs;
+ *  - TSM2_BATCH_CONCURRENT: one launch per class, concurrently on SM shares
+ *    (tsm2_batch_plan_set_grids; by default proportional to their bytes).
+ * A whole batch can be replayed as one CUDA graph launch.  Results do not
+ * depend on the mode, the variant's timing or the grid: every sum runs in a
+ * fixed order. */
 
 typedef struct tsm2_problem_s {
     char op;             /* 'r' (TSM2R schedule) or 'l' (TSM2L: n, k <= 64) */
@@ -274,48 +283,69 @@ typedef struct tsm2_problem_s {
 
 typedef struct tsm2_batch_plan_s *tsm2_batch_plan_t;
 
-/* Plan flags (tile choices offered to the autotuner). */
-#define TSM2_BATCH_WIDE_L 1   /* TSM2L problems: 8 rows per lane (else 4) */
-#define TSM2_BATCH_MERGE_R 2  /* all TSM2R problems in one class (C columns padded to 16) */
-#define TSM2_BATCH_MERGE_L 4  /* all TSM2L problems in one class (padded to 32) */
+/* Plan flags. */
+#define TSM2_BATCH_WIDE_L 1   /* accepted and ignored (rows per lane come from the tile variant) */
+#define TSM2_BATCH_MERGE_R 2  /* TSM2R column chunks all in the widest TSM2R class (16 columns) */
+#define TSM2_BATCH_MERGE_L 4  /* TSM2L column chunks all in the widest TSM2L class (32 columns) */
+#define TSM2_BATCH_VARIANT(v) ((v) << 8)  /* tile variant v in [0, tsm2_batch_num_variants()) */
+
+/* Execution modes (tsm2_batch_plan_set_mode). */
+#define TSM2_BATCH_CONCURRENT 0
+#define TSM2_BATCH_SERIAL 1
+#define TSM2_BATCH_SINGLE_LAUNCH 2
 
 /* Validates the problems (argument rules of tsm2r_s; additionally every A,
  * and B of TSM2R problems, must be 16-byte aligned with 16-byte multiple
  * leading-dimension strides, and TSM2L problems need n <= 64 and k <= 64
  * because batched TSM2L classes hold B on chip: TSM2_ERR_UNSUPPORTED
- * otherwise; the single-problem tsm2l_s has no such limit), encodes their
- * tensor maps and uploads the plan's tables and workspace (cudaMalloc: make
- * plans outside timed or captured regions).  The operand pointers are
- * recorded: the plan computes on whatever those buffers hold at execution.
- * Problems with k > 16 (TSM2R) or k > 32 (TSM2L) are split into column
- * groups.  *out receives the plan. */
+ * otherwise; the single-problem tsm2l_s has no such limit;
+ * TSM2_ERR_INVALID_VALUE for an unknown tile variant), encodes their tensor
+ * maps and uploads the plan's tables and workspace (cudaMalloc: make plans
+ * outside timed or captured regions).  The operand pointers are recorded:
+ * the plan computes on whatever those buffers hold at execution.  Problems
+ * with k > 16 (TSM2R) or k > 32 (TSM2L) are split into column groups.  *out
+ * receives the plan (mode TSM2_BATCH_SINGLE_LAUNCH). */
 tsm2_status tsm2_batch_plan_create_s(int nprob, const tsm2_problem_s *probs, int flags,
                                      tsm2_batch_plan_t *out);
 
-/* Runs every problem of the plan on `stream` (class kernels forked onto
- * internal streams and joined back).  Plans must not run concurrently with
- * themselves (their workspace is shared). */
+/* Runs every problem of the plan on `stream` in the plan's mode.  Plans must
+ * not run concurrently with themselves (their workspace is shared). */
 tsm2_status tsm2_batch_plan_execute(tsm2_batch_plan_t plan, void *stream);
 
 /* Runs only class `cls` on `stream`, on all SMs (used to measure classes). */
 tsm2_status tsm2_batch_plan_execute_class(tsm2_batch_plan_t plan, int cls, void *stream);
 
 /* Captures tsm2_batch_plan_execute once into a CUDA graph, on a stream the
- * plan owns (re-captured after tsm2_batch_plan_set_grids), and launches the
- * graph on `stream` (any stream, including the legacy default stream 0). */
+ * plan owns (re-captured after any change of mode, grids or shares), and
+ * launches the graph on `stream` (any stream, including the legacy default
+ * stream 0). */
 tsm2_status tsm2_batch_plan_graph_launch(tsm2_batch_plan_t plan, void *stream);
 
 int tsm2_batch_plan_num_classes(tsm2_batch_plan_t plan);
 tsm2_status tsm2_batch_plan_class_info(tsm2_batch_plan_t plan, int cls, const char **name, double *bytes,
                                        int *grid, int *nprob);
 
-/* Sets the number of persistent blocks of every class (each in [1, #SMs]). */
+/* Sets the number of persistent blocks of every class in the concurrent mode
+ * (each in [1, #SMs]). */
 tsm2_status tsm2_batch_plan_set_grids(tsm2_batch_plan_t plan, int ncls, const int *grids);
 
-/* serial != 0: tsm2_batch_plan_execute runs the classes one after another on
- * `stream`, each on all SMs (as tsm2_batch_plan_execute_class), instead of
- * concurrently on their SM shares.  Default 0. */
+/* serial != 0: mode TSM2_BATCH_SERIAL, else TSM2_BATCH_CONCURRENT. */
 tsm2_status tsm2_batch_plan_set_serial(tsm2_batch_plan_t plan, int serial);
+
+/* Execution mode: TSM2_BATCH_SINGLE_LAUNCH, TSM2_BATCH_SERIAL or
+ * TSM2_BATCH_CONCURRENT (TSM2_ERR_INVALID_VALUE otherwise). */
+tsm2_status tsm2_batch_plan_set_mode(tsm2_batch_plan_t plan, int mode);
+
+/* Blocks of the single launch, in [1, #SMs] (default #SMs). */
+tsm2_status tsm2_batch_plan_set_single_grid(tsm2_batch_plan_t plan, int grid);
+
+/* Kernel launches of one execution in the plan's current mode. */
+int tsm2_batch_plan_num_launches(tsm2_batch_plan_t plan);
+
+/* Compiled tile variants and their parameters. */
+int tsm2_batch_num_variants(void);
+tsm2_status tsm2_batch_variant_info(int variant, const char **name, int *stages, int *rows_per_lane,
+                                    int *inner_per_warp);
 
 void tsm2_batch_plan_destroy(tsm2_batch_plan_t plan);
 
@@ -336,8 +366,12 @@ void tsm2_shutdown(void);
 /* ---- Tuning and debugging knobs (process-wide, not thread-safe) ---------- */
 
 /* Upper bound, in nanoseconds, of every pipeline wait inside the kernels
- * (default 1e9).  0 means a single attempt, which forces the timeout path;
- * used by tests of the error path. */
+ * (default 1e9).  0 means a single attempt (which the hardware may suspend
+ * briefly, so a wait can still succeed); a negative value makes every wait
+ * give up at once without testing its barrier, which drives each kernel's
+ * timeout path deterministically.  Both are for tests of the error path;
+ * copies already issued are always waited for (up to 4 s) before a block
+ * exits. */
 void tsm2_set_wait_budget_ns(int64_t ns);
 
 /* Kernel path selection: 0 = automatic (default), 1 = always the

@@ -79,6 +79,17 @@ def _load():
             lib.tsm2_batch_plan_set_grids.restype = i32
             lib.tsm2_batch_plan_set_serial.argtypes = [vp, i32]
             lib.tsm2_batch_plan_set_serial.restype = i32
+            lib.tsm2_batch_plan_set_mode.argtypes = [vp, i32]
+            lib.tsm2_batch_plan_set_mode.restype = i32
+            lib.tsm2_batch_plan_set_single_grid.argtypes = [vp, i32]
+            lib.tsm2_batch_plan_set_single_grid.restype = i32
+            lib.tsm2_batch_plan_num_launches.argtypes = [vp]
+            lib.tsm2_batch_plan_num_launches.restype = i32
+            lib.tsm2_batch_num_variants.argtypes = []
+            lib.tsm2_batch_num_variants.restype = i32
+            lib.tsm2_batch_variant_info.argtypes = [i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i32),
+                                                    ctypes.POINTER(i32), ctypes.POINTER(i32)]
+            lib.tsm2_batch_variant_info.restype = i32
             lib.tsm2_batch_plan_destroy.argtypes = [vp]
             lib.tsm2_batch_plan_destroy.restype = None
             lib.tsm2_get_last_error_string.restype = ctypes.c_char_p

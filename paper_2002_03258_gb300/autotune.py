@@ -1,15 +1,24 @@
-"""Measurement-driven tuning of batched plans.
+"""Measurement-driven tuning of batched plans, seeded by the paper's model.
 
-The paper chooses t1 and tcf by offline profiling and t2, t3 with its model
-(Algorithm 7, Sec. 3.1.9; tcf in Sec. 3.2.2).  Here the free choices of a
-batch are (a) the tile classes -- 4 or 8 rows per lane for TSM2L problems,
-one merged or one class per C-column width -- and (b) the SM share of every
-class kernel (the classes run concurrently).  The tuner measures each class
-alone on the whole GPU (time t_c), sets the shares proportional to t_c (so
-all classes finish together if their time scales inversely with their SMs),
-compares that against the byte-proportional default, repeats for every tile
-choice and keeps the fastest, caching the result as JSON keyed by device and
-problem set.
+The paper chooses its tile parameters t1, t3 (and tcf for TSM2L) by offline
+profiling and t2 with its analytic model (Algorithm 7, Sec. 3.1.8-3.1.9;
+tcf in Sec. 3.2.2).  The free choices of a batch here are:
+
+* the tile variant: one of the compiled kernels, which differ in pipeline
+  stages, rows of C per lane and inner columns per warp and stage;
+* the class set: every column chunk in the narrowest class that holds it, or
+  all TSM2R chunks in the 16-column class and all TSM2L chunks in the
+  32-column class (fewer classes, padded columns);
+* the execution mode: one persistent launch for the whole batch, one launch
+  per class on all SMs, or the classes concurrently on SM shares.
+
+The first candidate timed is the model's choice (``seed_candidate``): the
+variant whose pipeline keeps Little's-law bytes in flight per SM with the
+most rows per lane, the merged class set when every merged width stays below
+the paper's t2 threshold (so padding costs no time in the model), and the
+single launch.  Then every candidate is timed (CUDA events, median of `reps`
+after a warm-up, L2 flushed before each), the fastest is kept and cached as
+JSON keyed by device and problem set.
 """
 from __future__ import annotations
 
@@ -19,9 +28,15 @@ import os
 import statistics
 import tempfile
 
-from .batched import MERGE_L, MERGE_R, WIDE_L, BatchPlan
+from . import perfmodel
+from .batched import MERGE_L, MERGE_R, BatchPlan, num_variants, variant_flag, variant_info
 
-FLAG_CHOICES = (0, WIDE_L, MERGE_R | MERGE_L, WIDE_L | MERGE_R | MERGE_L)
+FLAG_CHOICES = (0, MERGE_R | MERGE_L)
+MODE_CHOICES = ("single", "serial")
+WIDEST = {"r": 16, "l": 32}  # widest TSM2R / TSM2L class of every variant
+# Assumed DRAM round-trip latency (SM cycles) for the Little's-law estimate;
+# the paper leaves it a platform constant (Sec. 3.1.8).
+LATENCY_CYCLES = 1000.0
 
 
 def _time(fn, torch, stream, reps, flush=None):
@@ -44,6 +59,40 @@ def shares_from_times(times, sm_count):
     left = max(sm_count - n, 0)
     tot = sum(times) or 1.0
     return [1 + int(left * t / tot) for t in times]
+
+
+def stage_bytes(info) -> int:
+    """Bytes of A per pipeline stage of the TSM2R classes of a variant:
+    (32 lanes x rows per lane) rows x (8 warps x inner columns) x 4 bytes."""
+    return 32 * info["rows_per_lane"] * 8 * info["inner_per_warp"] * 4
+
+
+def in_flight_bytes(info) -> int:
+    """Bytes of A a block keeps in flight: every stage but the one consumed."""
+    return (info["stages"] - 1) * stage_bytes(info)
+
+
+def seed_candidate(infos, gpu: perfmodel.Gpu, latency_cycles: float = LATENCY_CYCLES):
+    """The model's choice (variant, flags, mode) among ``infos`` (variant_info
+    dicts) for a binary32 batch on ``gpu``."""
+    need = perfmodel.bytes_in_flight_per_sm(gpu.bw_gbs, gpu.sms, gpu.clock_ghz, latency_cycles)
+    ok = [i for i in infos if in_flight_bytes(i) >= need]
+    if ok:
+        best = max(ok, key=lambda i: (i["rows_per_lane"], i["stages"], -i["variant"]))
+    else:
+        best = max(infos, key=lambda i: (in_flight_bytes(i), -i["variant"]))
+    thr = perfmodel.t2_threshold(gpu.peak_gflops, gpu.bw_gbs, 4)
+    flags = MERGE_R | MERGE_L if max(WIDEST.values()) <= thr else 0
+    return best["variant"], flags, "single"
+
+
+def candidates(nvariants, seed=None):
+    """Every (variant, flags, mode), the seed first."""
+    out = [(v, f, m) for v in range(nvariants) for f in FLAG_CHOICES for m in MODE_CHOICES]
+    if seed is not None and seed in out:
+        out.remove(seed)
+        out.insert(0, seed)
+    return out
 
 
 def load_cache(path):
@@ -84,51 +133,69 @@ def problem_set_key(problems) -> str:
     return h.hexdigest()[:16]
 
 
-def autotune(problems, flags_choices=FLAG_CHOICES, reps=3, flush=None, cache_path=None, log=None):
+def device_model(torch, dev, hbm_gbs=None, fp32_gflops=None) -> perfmodel.Gpu:
+    """The model's platform constants for this GPU: SMs and clock from the
+    device, bandwidth and binary32 FMA peak measured (or, if not given, the
+    nominal 152 SMs x 128 lanes x 2 flops x clock and 8 TB/s)."""
+    props = torch.cuda.get_device_properties(dev)
+    clock_ghz = (getattr(props, "clock_rate", 0) or 2070000) / 1e6
+    sms = props.multi_processor_count
+    peak = fp32_gflops or sms * 128 * 2 * clock_ghz
+    return perfmodel.Gpu(props.name, peak, hbm_gbs or 8000.0, sms=sms, clock_ghz=clock_ghz)
+
+
+def make_plan(problems, variant, flags, mode):
+    plan = BatchPlan(problems, flags | variant_flag(variant))
+    plan.set_mode(mode)
+    return plan
+
+
+def autotune(problems, reps=3, flush=None, cache_path=None, log=None, hbm_gbs=None, fp32_gflops=None,
+             candidate_list=None):
     """Returns (plan, record): the fastest plan found and what was measured."""
     import torch
     dev = torch.cuda.current_device()
     props = torch.cuda.get_device_properties(dev)
-    sm = props.multi_processor_count
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     key = f"{props.name}|{problem_set_key(problems)}"
     cache = load_cache(cache_path)
     if key in cache:
         rec = cache[key]
-        plan = BatchPlan(problems, rec["flags"])
-        plan.set_grids(rec["grids"])
-        plan.set_serial(rec.get("serial", False))
-        return plan, dict(rec, cached=True)
+        return make_plan(problems, rec["variant"], rec["flags"], rec["mode"]), dict(rec, cached=True)
+    infos = [variant_info(v) for v in range(num_variants())]
+    gpu = device_model(torch, dev, hbm_gbs, fp32_gflops)
+    seed = seed_candidate(infos, gpu)
     best = None
     trials = []
-    for flags in flags_choices:
-        plan = BatchPlan(problems, flags)
-        plan.execute(sh)  # warm-up (module load, attributes)
+    for (v, flags, mode) in (candidate_list or candidates(len(infos), seed)):
+        plan = make_plan(problems, v, flags, mode)
+        plan.graph_launch(sh)  # warm-up: module load, attributes, graph capture
         torch.cuda.synchronize()
-        cls = plan.classes()
-        times = [_time(lambda i=i: plan.execute_class(i, sh), torch, stream, reps, flush) for i in range(len(cls))]
-        for label, grids in (("bytes", [c["grid"] for c in cls]), ("measured", shares_from_times(times, sm)),
-                             ("serial", [c["grid"] for c in cls])):
-            plan.set_serial(label == "serial")
-            plan.set_grids(grids)
-            plan.graph_launch(sh)
-            torch.cuda.synchronize()
-            t = _time(lambda: plan.graph_launch(sh), torch, stream, reps, flush)
-            trials.append({"flags": flags, "shares": label, "grids": grids, "ms": round(t, 4),
-                           "class_alone_ms": [round(x, 4) for x in times], "classes": [c["name"] for c in cls]})
-            if log:
-                log(trials[-1])
-            if best is None or t < best[0]:
-                if best is not None and best[1] is not plan:
-                    best[1].close()
-                best = (t, plan, flags, grids, label == "serial")
-        if best[1] is not plan:
+        t = _time(lambda: plan.graph_launch(sh), torch, stream, reps, flush)
+        trial = {"variant": v, "stages": infos[v]["stages"], "rows_per_lane": infos[v]["rows_per_lane"],
+                 "inner_per_warp": infos[v]["inner_per_warp"], "flags": flags, "mode": mode,
+                 "launches": plan.num_launches(), "classes": [c["name"] for c in plan.classes()],
+                 "ms": round(t, 4), "seed": (v, flags, mode) == seed}
+        trials.append(trial)
+        if log:
+            log(trial)
+        if best is None or t < best[0]:
+            if best is not None:
+                best[1].close()
+            best = (t, plan, trial)
+        else:
             plan.close()
-    t, plan, flags, grids, serial = best
-    plan.set_grids(grids)
-    plan.set_serial(serial)
-    rec = {"flags": flags, "grids": grids, "serial": serial, "ms": round(t, 4), "trials": trials}
+    t, plan, trial = best
+    rank = sorted(x["ms"] for x in trials).index(next(x["ms"] for x in trials if x["seed"])) + 1 \
+        if any(x["seed"] for x in trials) else None
+    rec = {"variant": trial["variant"], "flags": trial["flags"], "mode": trial["mode"], "ms": round(t, 4),
+           "launches": trial["launches"], "seed": {"variant": seed[0], "flags": seed[1], "mode": seed[2],
+                                                   "rank": rank},
+           "model": {"bytes_in_flight_per_sm": round(perfmodel.bytes_in_flight_per_sm(
+               gpu.bw_gbs, gpu.sms, gpu.clock_ghz, LATENCY_CYCLES)), "t2_threshold_fp32": round(
+               perfmodel.t2_threshold(gpu.peak_gflops, gpu.bw_gbs, 4), 2), "latency_cycles": LATENCY_CYCLES},
+           "trials": trials}
     if cache_path:
-        store_cache(cache_path, key, {"flags": flags, "grids": grids, "serial": serial, "ms": round(t, 4)})
+        store_cache(cache_path, key, {k: rec[k] for k in ("variant", "flags", "mode", "ms", "launches")})
     return plan, rec

@@ -1,10 +1,11 @@
 """Batches of uneven TSM2R / TSM2L problems (binary32): Python wrapper over
 the ``tsm2_batch_plan_*`` C ABI.
 
-A plan groups the problems into tile classes; each class is one persistent
-kernel over all of its problems, the classes run concurrently on SM shares
-(or one after another on all SMs), and the whole batch can be replayed as one
-CUDA graph launch.
+A plan groups the problems into tile classes of one compiled tile variant.
+By default the whole batch runs as ONE persistent kernel launch whose blocks
+walk their share of every class in turn; the classes can also run one after
+another (one launch each, on all SMs) or concurrently on SM shares.  Any mode
+can be replayed as one CUDA graph launch.
 """
 from __future__ import annotations
 
@@ -12,9 +13,34 @@ import ctypes
 
 from . import _load, check
 
-WIDE_L = 1
+WIDE_L = 1  # accepted and ignored
 MERGE_R = 2
 MERGE_L = 4
+
+CONCURRENT = 0
+SERIAL = 1
+SINGLE_LAUNCH = 2
+MODES = {"concurrent": CONCURRENT, "serial": SERIAL, "single": SINGLE_LAUNCH}
+
+
+def variant_flag(v: int) -> int:
+    """Plan flag selecting tile variant ``v``."""
+    return int(v) << 8
+
+
+def num_variants() -> int:
+    return int(_load().tsm2_batch_num_variants())
+
+
+def variant_info(v: int) -> dict:
+    """Tile parameters of compiled variant ``v``."""
+    lib = _load()
+    name = ctypes.c_char_p()
+    st, rows, inner = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib.tsm2_batch_variant_info(v, ctypes.byref(name), ctypes.byref(st), ctypes.byref(rows),
+                                      ctypes.byref(inner)))
+    return {"variant": v, "name": name.value.decode(), "stages": st.value, "rows_per_lane": rows.value,
+            "inner_per_warp": inner.value}
 
 
 class Problem(ctypes.Structure):
@@ -37,6 +63,7 @@ class BatchPlan:
         check(lib.tsm2_batch_plan_create_s(len(problems), ctypes.cast(arr, ctypes.c_void_p), flags, ctypes.byref(out)))
         self.handle = out
         self.flags = flags
+        self.variant = (flags >> 8) & 0xFF
 
     def execute(self, stream=0):
         check(_load().tsm2_batch_plan_execute(self.handle, stream))
@@ -66,6 +93,16 @@ class BatchPlan:
 
     def set_serial(self, serial: bool):
         check(_load().tsm2_batch_plan_set_serial(self.handle, int(bool(serial))))
+
+    def set_mode(self, mode):
+        """``mode``: SINGLE_LAUNCH, SERIAL, CONCURRENT or one of their names."""
+        check(_load().tsm2_batch_plan_set_mode(self.handle, MODES.get(mode, mode)))
+
+    def set_single_grid(self, grid: int):
+        check(_load().tsm2_batch_plan_set_single_grid(self.handle, int(grid)))
+
+    def num_launches(self) -> int:
+        return int(_load().tsm2_batch_plan_num_launches(self.handle))
 
     def close(self):
         if self.handle:

@@ -84,11 +84,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Waits until the phase with parity `parity` of `bar` has completed, for at
-// most `budget_ns` nanoseconds (0: a single attempt), giving up early when
-// `*abort` becomes non-zero.  Returns false on timeout or abort; the caller
-// records it and stops using the pipeline.
+// most `budget_ns` nanoseconds (0: a single attempt, which the hardware may
+// itself suspend for a short while), giving up early when `*abort` becomes
+// non-zero.  A negative budget gives up at once without testing the barrier
+// (a test hook: it drives every kernel's timeout path deterministically).
+// Returns false on timeout or abort; the caller records it and stops using
+// the pipeline.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int64_t budget_ns,
                                                   const volatile int *abort = nullptr) {
+    if (budget_ns < 0) return false;
     if (mbar_try_wait(bar, parity)) return true;
     if (budget_ns <= 0) return false;
     const uint64_t t0 = globaltimer_ns();

@@ -45,7 +45,6 @@ struct StreamShape {
     int BOXM;        // rows per TMA box
     int gran_rows;   // 1: split inner dim at stage granularity; 0: whole row blocks
     bool b_resident; // B loaded once into shared memory (requires n <= n_max_resident)
-    bool b_rowmajor; // streamed B read from its packed transpose (bt_pack_launch)
     int n_max_resident;
     int smem_bytes;
     int threads;
@@ -55,13 +54,6 @@ struct StreamShape {
 // Returns nullptr if no compiled configuration covers (elem, op, kc).
 const StreamShape *stream_shape(int elem, char op, int kc);
 cudaError_t stream_launch(const StreamShape *shape, const StreamLaunch &L, cudaStream_t stream);
-
-// Packs the first k (<= kc) columns of B (n x k, column-major, ldb) into Bt,
-// n rows of kc elements (Bt[j*kc + c] = B[j + c*ldb], zero for c >= k), the
-// layout read by configurations with b_rowmajor.  Bt must hold n*kc elements
-// and be 16-byte aligned.
-cudaError_t bt_pack_launch(int elem, int64_t n, int k, const void *B, int64_t ldb, int kc, void *Bt,
-                           cudaStream_t stream);
 
 // Copies `cols` columns of `row_bytes` bytes (column c at src + c*lds_bytes,
 // dst + c*ldd_bytes) with the SMs' loads and stores; either side may be a
@@ -135,33 +127,52 @@ cudaError_t split_bf16_launch(int64_t rows, int64_t cols, const float *X, int64_
 // Device-side descriptor of one problem of a batch class.
 struct ProbDesc {  // aligned as its tensor maps
     CUtensorMap mapA;      // A: dims {m, n}, box {BOXM, BNS}
-    CUtensorMap mapB;      // TSM2R classes: B dims {n, k}, box {BNS, KC}; row-major classes: Bt dims {KC, n}, box {KC, BNS}
+    CUtensorMap mapB;      // TSM2R classes: B dims {n, k}, box {BNS, KC} (column-major)
     int64_t m, n, ldb, ldc;
-    const void *B;         // TSM2L classes read B with ordinary loads; row-major TSM2R classes pack it
-    void *Bt;              // row-major TSM2R classes: packed n x KC copy of B (plan workspace)
+    const void *B;         // TSM2L classes read B with ordinary loads
     void *C;
     int64_t group_begin;   // first work group of the problem in the class numbering
     int64_t rb_begin;      // first row block (counters and partial-sum slots)
     int32_t k, upr, gran, c_vec;
 };
-struct BatchLaunch {
+
+// Classes per batch kernel (tsm2_batch_kernel.cuh) and its launch arguments.
+constexpr int kMaxBatchMenu = 8;
+
+// Per-class arguments of one batch-kernel launch.
+struct ClassParams {
     const ProbDesc *probs;
     int nprob;
-    int64_t ngroups;
-    void *ws;
-    int *counters;
+    int64_t ngroups;  // 0: the class has no work in this launch
+    float *ws;        // partial-sum slots: (grid + row blocks) x KC x BM
+    int *counters;    // one arrival counter per row block, zero between launches
+};
+
+struct BatchKParams {
+    ClassParams cls[kMaxBatchMenu];  // slot i of the kernel's menu
     unsigned *status;
     int64_t wait_ns;
-    int grid;
 };
+
 struct BatchClass {
-    char op;  // 'r' TSM2R, 'l' TSM2L, 'w' TSM2L with 8 rows per lane
+    char op;  // 'r' TSM2R schedule, 'w' TSM2L schedule (whole row blocks, B resident)
     const char *name;
     int KC, BM, BNS, BOXM;
-    bool b_rowmajor;  // TSM2R class reading B from packed row-major copies (ProbDesc::Bt)
-    cudaError_t (*launch)(const BatchLaunch &, cudaStream_t);
+    int stages, rows_per_lane;
 };
-const BatchClass *batch_class(char op, int kc);
+
+// A tile variant: the classes one batch kernel holds (its "menu") and the
+// launch of that kernel.  Every class of a plan is a slot of its menu; a
+// launch runs any subset of the slots (empty slots have no work).
+struct BatchMenu {
+    const char *name;   // tile variant, e.g. "v0 stages5 rows8 inner4"
+    int stages, rows_per_lane, inner_per_warp;
+    int nslots;
+    const BatchClass *slots[kMaxBatchMenu];
+    cudaError_t (*launch)(const BatchKParams &, int grid, cudaStream_t);
+};
+int batch_menu_count();
+const BatchMenu *batch_menu(int variant);
 
 // Work partition of the persistent grid (shared by host sizing and kernels).
 struct Partition {

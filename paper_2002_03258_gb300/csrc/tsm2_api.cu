@@ -295,7 +295,7 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
         L.g = g;
         st = encode_2d(&L.mapA, elem, A, m, n, lda, shape->BOXM, shape->BNS);
         if (st != TSM2_SUCCESS) return st;
-        if (!shape->b_resident && !shape->b_rowmajor) {
+        if (!shape->b_resident) {
             st = encode_2d(&L.mapB, elem, g.B, n, g.k, ldb, shape->BNS, shape->KC);
             if (st != TSM2_SUCCESS) return st;
         }
@@ -317,19 +317,10 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
         L.grid = (int)grid;
         void *ws = nullptr;
         int *counters = nullptr;
-        if (!shape->b_resident) {
-            const size_t slots = whole ? 0 : (size_t)(grid + num_rb) * shape->KC * shape->BM * elem;
-            const size_t bt_off = (slots + 255) / 256 * 256;
-            const size_t bt_bytes = shape->b_rowmajor ? (size_t)n * shape->KC * elem : 0;
-            st = workspace(stream, (size_t)num_rb * sizeof(int), bt_off + bt_bytes, &ws, &counters);
+        if (!shape->b_resident && !whole) {
+            const size_t slots = (size_t)(grid + num_rb) * shape->KC * shape->BM * elem;
+            st = workspace(stream, (size_t)num_rb * sizeof(int), slots, &ws, &counters);
             if (st != TSM2_SUCCESS) return st;
-            if (shape->b_rowmajor) {
-                void *bt = static_cast<char *>(ws) + bt_off;
-                e = bt_pack_launch(elem, n, g.k, g.B, ldb, shape->KC, bt, stream);
-                if (e != cudaSuccess) return cuda_error(e, "B packing kernel launch");
-                st = encode_2d(&L.mapB, elem, bt, shape->KC, n, shape->KC, shape->KC, shape->BNS);
-                if (st != TSM2_SUCCESS) return st;
-            }
         }
         L.ws = ws;
         L.counters = counters;
@@ -575,13 +566,14 @@ tsm2_status gemm_bf16(int64_t m, int64_t n, int64_t k, const void *A_hi, const v
 struct tsm2_batch_plan_s {
     struct Cls {
         const tsm2::BatchClass *cls = nullptr;
+        int slot = 0;             // slot of the class in the menu's kernel
         std::vector<tsm2::ProbDesc> host;
         int64_t ngroups = 0, nrb = 0;
         double bytes = 0;
         tsm2::ProbDesc *d_probs = nullptr;
         void *d_ws = nullptr;     // counters, then partial-sum slots
         size_t counter_bytes = 0;
-        int grid = 1;
+        int grid = 1;             // blocks of the class in the concurrent mode
         cudaStream_t aux = nullptr;
         cudaEvent_t done = nullptr;
     };
@@ -591,20 +583,31 @@ struct tsm2_batch_plan_s {
     };
     int dev = 0;
     int sm_count = 0;
+    int variant = 0;
+    const tsm2::BatchMenu *menu = nullptr;
+    int mode = TSM2_BATCH_SINGLE_LAUNCH;
+    int single_grid = 0;             // blocks of the single launch
     std::vector<Cls> classes;
     std::vector<Zero> zeros;
     cudaEvent_t fork = nullptr;
     cudaGraphExec_t graph = nullptr;
     cudaStream_t capture = nullptr;  // private stream the graph is captured on
-    bool serial = false;             // classes one after another, each on all SMs
     double total_bytes = 0;
 };
 
 namespace tsm2 {
 namespace {
 
+// Live plans, so that a timeout can reset their arrival counters.
+std::mutex g_plans_mu;
+std::vector<tsm2_batch_plan_s *> g_plans;
+
 void destroy_plan(tsm2_batch_plan_s *P) {
     if (!P) return;
+    {
+        std::lock_guard<std::mutex> lk(g_plans_mu);
+        g_plans.erase(std::remove(g_plans.begin(), g_plans.end(), P), g_plans.end());
+    }
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(P->dev);
@@ -621,48 +624,76 @@ void destroy_plan(tsm2_batch_plan_s *P) {
     delete P;
 }
 
-tsm2_status plan_execute(tsm2_batch_plan_s *P, cudaStream_t stream, int only) {
-    cudaError_t e;
-    if (only < 0)
-        for (const auto &z : P->zeros) {
-            e = cudaMemset2DAsync(z.C, (size_t)z.ldc * 4, 0, (size_t)z.m * 4, (size_t)z.k, stream);
-            if (e != cudaSuccess) return cuda_error(e, "cudaMemset2DAsync");
-        }
+// Arrival counters of every live plan on device `dev` back to zero (after a
+// launch that gave up, they may be left non-zero).
+void reset_plan_counters(int dev) {
+    std::lock_guard<std::mutex> lk(g_plans_mu);
+    for (tsm2_batch_plan_s *P : g_plans)
+        if (P->dev == dev)
+            for (auto &c : P->classes)
+                if (c.d_ws) cudaMemset(c.d_ws, 0, c.counter_bytes);
+}
+
+void class_params(const tsm2_batch_plan_s::Cls &c, ClassParams &cp) {
+    cp.probs = c.d_probs;
+    cp.nprob = (int)c.host.size();
+    cp.ngroups = c.ngroups;
+    cp.counters = static_cast<int *>(c.d_ws);
+    cp.ws = reinterpret_cast<float *>(static_cast<char *>(c.d_ws) + c.counter_bytes);
+}
+
+// One launch of the plan's batch kernel over the classes [lo, hi) (all
+// other slots empty) on `grid` blocks.
+tsm2_status launch_classes(tsm2_batch_plan_s *P, int lo, int hi, int grid, cudaStream_t stream) {
     DeviceState *dev = nullptr;
     tsm2_status st = device_state(&dev);
     if (st != TSM2_SUCCESS) return st;
+    BatchKParams kp;
+    std::memset(&kp, 0, sizeof kp);
+    for (int i = lo; i < hi; ++i) class_params(P->classes[i], kp.cls[P->classes[i].slot]);
+    kp.status = dev->status;
+    kp.wait_ns = g_wait_ns;
+    const cudaError_t e = P->menu->launch(kp, grid < 1 ? 1 : grid, stream);
+    return e == cudaSuccess ? TSM2_SUCCESS : cuda_error(e, "batch kernel launch");
+}
+
+int class_grid_alone(const tsm2_batch_plan_s *P, int i) {
+    return (int)std::min<int64_t>(P->sm_count, P->classes[i].ngroups);
+}
+
+tsm2_status plan_execute(tsm2_batch_plan_s *P, cudaStream_t stream, int only) {
+    cudaError_t e;
     const int nc = (int)P->classes.size();
-    if (only < 0 && P->serial) {
+    if (only >= 0) return launch_classes(P, only, only + 1, class_grid_alone(P, only), stream);
+    for (const auto &z : P->zeros) {
+        e = cudaMemset2DAsync(z.C, (size_t)z.ldc * 4, 0, (size_t)z.m * 4, (size_t)z.k, stream);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMemset2DAsync");
+    }
+    if (nc == 0) return TSM2_SUCCESS;
+    if (P->mode == TSM2_BATCH_SINGLE_LAUNCH) return launch_classes(P, 0, nc, P->single_grid, stream);
+    if (P->mode == TSM2_BATCH_SERIAL) {
         for (int i = 0; i < nc; ++i) {
-            tsm2_status s = plan_execute(P, stream, i);
+            tsm2_status s = launch_classes(P, i, i + 1, class_grid_alone(P, i), stream);
             if (s != TSM2_SUCCESS) return s;
         }
         return TSM2_SUCCESS;
     }
-    if (only < 0 && nc > 1) {
+    // Concurrent: every class on its own SM share, forked onto the plan's
+    // streams and joined back.
+    if (nc > 1) {
         e = cudaEventRecord(P->fork, stream);
         if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
     }
     for (int i = 0; i < nc; ++i) {
-        if (only >= 0 && i != only) continue;
         auto &c = P->classes[i];
-        cudaStream_t s = (only >= 0 || i == 0) ? stream : c.aux;
-        if (only < 0 && i > 0) {
+        cudaStream_t s = i == 0 ? stream : c.aux;
+        if (i > 0) {
             e = cudaStreamWaitEvent(s, P->fork, 0);
             if (e != cudaSuccess) return cuda_error(e, "cudaStreamWaitEvent");
         }
-        BatchLaunch L;
-        L.probs = c.d_probs;
-        L.nprob = (int)c.host.size();
-        L.ngroups = c.ngroups;
-        L.counters = static_cast<int *>(c.d_ws);
-        L.ws = static_cast<char *>(c.d_ws) + c.counter_bytes;
-        L.status = dev->status;
-        L.wait_ns = g_wait_ns;
-        L.grid = only >= 0 ? (int)std::min<int64_t>(P->sm_count, c.ngroups) : c.grid;
-        e = c.cls->launch(L, s);
-        if (e != cudaSuccess) return cuda_error(e, "batched kernel launch");
-        if (only < 0 && i > 0) {
+        tsm2_status st = launch_classes(P, i, i + 1, c.grid, s);
+        if (st != TSM2_SUCCESS) return st;
+        if (i > 0) {
             e = cudaEventRecord(c.done, s);
             if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
             e = cudaStreamWaitEvent(stream, c.done, 0);
@@ -768,30 +799,21 @@ tsm2_status gemm_r32_noalloc(int64_t m, int64_t n, int64_t k, const float *A, in
         if (grid > ngroups) grid = ngroups;
         if (grid < 1) grid = 1;
         const size_t counter_bytes = (size_t)num_rb * sizeof(int);
-        // Partial-sum slots, then (row-major configurations) the packed B.
+        // Partial-sum slots of split row blocks.
         const size_t slot_bytes = (size_t)(grid + num_rb) * shape->KC * shape->BM * elem;
-        const size_t bt_off = (slot_bytes + 255) / 256 * 256;
-        const size_t bt_bytes = shape->b_rowmajor ? (size_t)n * shape->KC * elem : 0;
         const size_t data_cap = kNoAllocScratchBytes - kNoAllocCounterBytes;
-        if (counter_bytes > kNoAllocCounterBytes || bt_off + bt_bytes > data_cap)
+        if (counter_bytes > kNoAllocCounterBytes || slot_bytes > data_cap)
             return set_error(TSM2_ERR_UNSUPPORTED,
-                             "%s: m=%lld n=%lld needs %zu bytes of counters and %zu bytes of partial sums and "
-                             "packed B; the static scratch holds %zu and %zu; use tsm2r_s instead",
-                             fn, (long long)m, (long long)n, counter_bytes, bt_off + bt_bytes, kNoAllocCounterBytes,
+                             "%s: m=%lld n=%lld needs %zu bytes of counters and %zu bytes of partial sums; "
+                             "the static scratch holds %zu and %zu; use tsm2r_s instead",
+                             fn, (long long)m, (long long)n, counter_bytes, slot_bytes, kNoAllocCounterBytes,
                              data_cap);
         StreamLaunch L;
         std::memset(&L, 0, sizeof L);
         L.g = g;
         st = encode_2d(&L.mapA, elem, A, m, n, lda, shape->BOXM, shape->BNS);
         if (st != TSM2_SUCCESS) return st;
-        if (shape->b_rowmajor) {
-            void *bt = static_cast<char *>(scratch) + kNoAllocCounterBytes + bt_off;
-            e = bt_pack_launch(elem, n, g.k, g.B, ldb, shape->KC, bt, stream);
-            if (e != cudaSuccess) return cuda_error(e, "B packing kernel launch");
-            st = encode_2d(&L.mapB, elem, bt, shape->KC, n, shape->KC, shape->KC, shape->BNS);
-        } else {
-            st = encode_2d(&L.mapB, elem, g.B, n, g.k, ldb, shape->BNS, shape->KC);
-        }
+        st = encode_2d(&L.mapB, elem, g.B, n, g.k, ldb, shape->BNS, shape->KC);
         if (st != TSM2_SUCCESS) return st;
         // The array keeps whatever the previous call left; the arrival
         // counters must start at zero.
@@ -1125,7 +1147,7 @@ tsm2_status tsm2_get_device_status(void *stream) {
     e = cudaMemcpyToSymbol(g_status_word, &zero, sizeof zero);
     if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyToSymbol(status)");
     // An abandoned launch may leave arrival counters non-zero: clear them all
-    // on this device.
+    // on this device (stream workspaces and batch plans).
     int dev = 0;
     cudaGetDevice(&dev);
     {
@@ -1133,6 +1155,7 @@ tsm2_status tsm2_get_device_status(void *stream) {
         for (auto &kv : g_ws)
             if (kv.first.first == dev && kv.second.ptr) cudaMemset(kv.second.ptr, 0, kv.second.counter_bytes);
     }
+    reset_plan_counters(dev);
     cudaDeviceSynchronize();
     return set_error(TSM2_ERR_TIMEOUT, "a pipeline wait exceeded its bound; the output of that call is undefined");
 }
@@ -1238,16 +1261,34 @@ tsm2_status tsm2_batch_plan_create_s(int nprob, const tsm2_problem_s *probs, int
     *out = nullptr;
     if (nprob < 0 || (nprob > 0 && !probs))
         return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_create_s: bad problem list");
+    const int variant = (flags >> 8) & 0xFF;
+    if (variant >= batch_menu_count())
+        return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_create_s: tile variant %d out of [0, %d)", variant,
+                         batch_menu_count());
     DeviceState *dev = nullptr;
     tsm2_status st = device_state(&dev);
     if (st != TSM2_SUCCESS) return st;
     tsm2_batch_plan_s *P = new tsm2_batch_plan_s();
     cudaGetDevice(&P->dev);
     P->sm_count = dev->sm_count;
-    const bool wide = (flags & TSM2_BATCH_WIDE_L) != 0;
+    P->single_grid = dev->sm_count;
+    P->variant = variant;
+    P->menu = batch_menu(variant);
     const bool merge_r = (flags & TSM2_BATCH_MERGE_R) != 0;
     const bool merge_l = (flags & TSM2_BATCH_MERGE_L) != 0;
-    std::map<const BatchClass *, int> index;
+    // Class of a column chunk: the narrowest slot of its schedule that holds
+    // kk columns (the widest with the merge flag).
+    auto slot_for = [&](char op, int kk) -> int {
+        int best = -1;
+        for (int t = 0; t < P->menu->nslots; ++t) {
+            const BatchClass *c = P->menu->slots[t];
+            if (c->op != op || c->KC < kk) continue;
+            const bool merge = op == 'r' ? merge_r : merge_l;
+            if (best < 0 || (merge ? c->KC > P->menu->slots[best]->KC : c->KC < P->menu->slots[best]->KC)) best = t;
+        }
+        return best;
+    };
+    std::map<int, int> index;  // slot -> class
     for (int i = 0; i < nprob; ++i) {
         const tsm2_problem_s &q = probs[i];
         const char op = q.op == 'l' ? 'l' : (q.op == 'r' ? 'r' : 0);
@@ -1278,30 +1319,25 @@ tsm2_status tsm2_batch_plan_create_s(int nprob, const tsm2_problem_s *probs, int
         const int kcmax = op == 'l' ? 32 : 16;
         for (int64_t c0 = 0; c0 < q.k; c0 += kcmax) {
             const int kk = (int)std::min<int64_t>(kcmax, q.k - c0);
-            int kc = kc_for(kk);
-            if (op == 'r' && merge_r) kc = 16;
-            if (op == 'l' && merge_l) kc = 32;
-            const BatchClass *cls = batch_class(op == 'l' && wide ? 'w' : op, kc);
-            if (!cls) {
+            const int slot = slot_for(op == 'l' ? 'w' : 'r', kk);
+            if (slot < 0) {
                 destroy_plan(P);
                 return set_error(TSM2_ERR_UNSUPPORTED, "batch problem %d: no class for k chunk %d", i, kk);
             }
-            auto it = index.find(cls);
+            const BatchClass *cls = P->menu->slots[slot];
+            auto it = index.find(slot);
             if (it == index.end()) {
-                index[cls] = (int)P->classes.size();
+                it = index.emplace(slot, (int)P->classes.size()).first;
                 P->classes.emplace_back();
                 P->classes.back().cls = cls;
-                it = index.find(cls);
+                P->classes.back().slot = slot;
             }
             auto &C = P->classes[it->second];
             ProbDesc d;
             std::memset(&d, 0, sizeof d);
             const float *Bc = q.B + c0 * q.ldb;
             st = encode_2d(&d.mapA, 4, q.A, q.m, q.n, q.lda, cls->BOXM, cls->BNS);
-            // Row-major classes encode B's map over the packed copy once the
-            // plan workspace exists (below).
-            if (st == TSM2_SUCCESS && op == 'r' && !cls->b_rowmajor)
-                st = encode_2d(&d.mapB, 4, Bc, q.n, kk, q.ldb, cls->BNS, cls->KC);
+            if (st == TSM2_SUCCESS && op == 'r') st = encode_2d(&d.mapB, 4, Bc, q.n, kk, q.ldb, cls->BNS, cls->KC);
             if (st != TSM2_SUCCESS) {
                 destroy_plan(P);
                 return st;
@@ -1326,29 +1362,17 @@ tsm2_status tsm2_batch_plan_create_s(int nprob, const tsm2_problem_s *probs, int
             C.host.push_back(d);
         }
     }
+    // Classes in menu order: the single launch walks them in this order.
+    std::sort(P->classes.begin(), P->classes.end(),
+              [](const tsm2_batch_plan_s::Cls &a, const tsm2_batch_plan_s::Cls &b) { return a.slot < b.slot; });
     cudaError_t e = cudaSuccess;
     for (auto &C : P->classes) {
         P->total_bytes += C.bytes;
         C.counter_bytes = ((size_t)C.nrb * sizeof(int) + 255) / 256 * 256;
+        // Partial-sum slots for grids of up to one block per SM (TSM2R
+        // classes split row blocks; TSM2L classes never do).
         const size_t slots = C.cls->op == 'r' ? (size_t)(P->sm_count + C.nrb) * C.cls->KC * C.cls->BM * 4 : 0;
-        // Row-major TSM2R classes: packed B copies after the partial-sum slots.
-        const size_t bt_base = C.counter_bytes + (slots + 255) / 256 * 256;
-        size_t bt_bytes = 0;
-        if (C.cls->b_rowmajor)
-            for (const auto &d : C.host) bt_bytes += ((size_t)d.n * C.cls->KC * 4 + 255) / 256 * 256;
-        if ((e = cudaMalloc(&C.d_ws, bt_base + bt_bytes + 256)) != cudaSuccess) break;
-        if (C.cls->b_rowmajor) {
-            size_t off = bt_base;
-            for (auto &d : C.host) {
-                d.Bt = static_cast<char *>(C.d_ws) + off;
-                off += ((size_t)d.n * C.cls->KC * 4 + 255) / 256 * 256;
-                tsm2_status s2 = encode_2d(&d.mapB, 4, d.Bt, C.cls->KC, d.n, C.cls->KC, C.cls->KC, C.cls->BNS);
-                if (s2 != TSM2_SUCCESS) {
-                    destroy_plan(P);
-                    return s2;
-                }
-            }
-        }
+        if ((e = cudaMalloc(&C.d_ws, C.counter_bytes + slots + 256)) != cudaSuccess) break;
         if ((e = cudaMalloc(&C.d_probs, C.host.size() * sizeof(ProbDesc))) != cudaSuccess) break;
         if ((e = cudaMemcpy(C.d_probs, C.host.data(), C.host.size() * sizeof(ProbDesc), cudaMemcpyHostToDevice)) !=
             cudaSuccess)
@@ -1363,17 +1387,21 @@ tsm2_status tsm2_batch_plan_create_s(int nprob, const tsm2_problem_s *probs, int
         destroy_plan(P);
         return cuda_error(e, "tsm2_batch_plan_create_s");
     }
-    // Default SM shares: proportional to each class's algorithmic bytes.
-    std::vector<double> w;
-    for (auto &C : P->classes) w.push_back(C.bytes);
-    std::vector<int> grids(w.size(), 1);
-    const int nc = (int)w.size();
+    // Default SM shares of the concurrent mode: proportional to each class's
+    // algorithmic bytes.
+    const int nc = (int)P->classes.size();
     if (nc > 0) {
         int left = std::max(P->sm_count - nc, 0);
         double tot = 0;
-        for (double x : w) tot += x;
-        for (int i = 0; i < nc; ++i) grids[i] += (int)((double)left * w[i] / (tot > 0 ? tot : 1));
-        for (int i = 0; i < nc; ++i) P->classes[i].grid = (int)std::min<int64_t>(grids[i], P->classes[i].ngroups);
+        for (auto &C : P->classes) tot += C.bytes;
+        for (auto &C : P->classes) {
+            const int g = 1 + (int)((double)left * C.bytes / (tot > 0 ? tot : 1));
+            C.grid = (int)std::min<int64_t>(g, C.ngroups);
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_plans_mu);
+        g_plans.push_back(P);
     }
     *out = P;
     return TSM2_SUCCESS;
@@ -1432,6 +1460,13 @@ tsm2_status tsm2_batch_plan_class_info(tsm2_batch_plan_t plan, int cls, const ch
     return TSM2_SUCCESS;
 }
 
+static void drop_graph(tsm2_batch_plan_t plan) {
+    if (plan->graph) {
+        cudaGraphExecDestroy(plan->graph);
+        plan->graph = nullptr;
+    }
+}
+
 tsm2_status tsm2_batch_plan_set_grids(tsm2_batch_plan_t plan, int ncls, const int *grids) {
     if (!plan || ncls != (int)plan->classes.size() || (ncls > 0 && !grids))
         return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_set_grids: bad arguments");
@@ -1442,26 +1477,53 @@ tsm2_status tsm2_batch_plan_set_grids(tsm2_batch_plan_t plan, int ncls, const in
     }
     for (int i = 0; i < ncls; ++i)
         plan->classes[i].grid = (int)std::min<int64_t>(grids[i], plan->classes[i].ngroups);
-    if (plan->graph) {
-        cudaGraphExecDestroy(plan->graph);
-        plan->graph = nullptr;
-    }
+    drop_graph(plan);
     return TSM2_SUCCESS;
 }
 
 tsm2_status tsm2_batch_plan_set_serial(tsm2_batch_plan_t plan, int serial) {
     if (!plan) return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_set_serial: NULL plan");
-    if (plan->serial != (serial != 0) && plan->graph) {
-        cudaGraphExecDestroy(plan->graph);
-        plan->graph = nullptr;
-    }
-    plan->serial = serial != 0;
+    return tsm2_batch_plan_set_mode(plan, serial ? TSM2_BATCH_SERIAL : TSM2_BATCH_CONCURRENT);
+}
+
+tsm2_status tsm2_batch_plan_set_mode(tsm2_batch_plan_t plan, int mode) {
+    if (!plan) return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_set_mode: NULL plan");
+    if (mode != TSM2_BATCH_CONCURRENT && mode != TSM2_BATCH_SERIAL && mode != TSM2_BATCH_SINGLE_LAUNCH)
+        return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_set_mode: unknown mode %d", mode);
+    if (plan->mode != mode) drop_graph(plan);
+    plan->mode = mode;
+    return TSM2_SUCCESS;
+}
+
+tsm2_status tsm2_batch_plan_set_single_grid(tsm2_batch_plan_t plan, int grid) {
+    if (!plan || grid < 1 || grid > plan->sm_count)
+        return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_plan_set_single_grid: bad plan or grid");
+    if (plan->single_grid != grid) drop_graph(plan);
+    plan->single_grid = grid;
+    return TSM2_SUCCESS;
+}
+
+int tsm2_batch_plan_num_launches(tsm2_batch_plan_t plan) {
+    if (!plan || plan->classes.empty()) return 0;
+    return plan->mode == TSM2_BATCH_SINGLE_LAUNCH ? 1 : (int)plan->classes.size();
+}
+
+int tsm2_batch_num_variants(void) { return batch_menu_count(); }
+
+tsm2_status tsm2_batch_variant_info(int variant, const char **name, int *stages, int *rows_per_lane,
+                                    int *inner_per_warp) {
+    const BatchMenu *m = (variant >= 0) ? batch_menu(variant) : nullptr;
+    if (!m) return set_error(TSM2_ERR_INVALID_VALUE, "tsm2_batch_variant_info: variant %d out of range", variant);
+    if (name) *name = m->name;
+    if (stages) *stages = m->stages;
+    if (rows_per_lane) *rows_per_lane = m->rows_per_lane;
+    if (inner_per_warp) *inner_per_warp = m->inner_per_warp;
     return TSM2_SUCCESS;
 }
 
 void tsm2_batch_plan_destroy(tsm2_batch_plan_t plan) { destroy_plan(plan); }
 
-void tsm2_set_wait_budget_ns(int64_t ns) { g_wait_ns = ns < 0 ? 0 : ns; }
+void tsm2_set_wait_budget_ns(int64_t ns) { g_wait_ns = ns < 0 ? -1 : ns; }
 
 void tsm2_set_path(int path) { g_path = path; }
 

@@ -40,6 +40,18 @@ struct Cfg {
     // so packed FMAs pair C columns and duplicate the A value (R per inner
     // index) instead of the B value (KCW per inner index).
     static constexpr bool BT = BT_;
+    // Streamed B read row-major is loaded by the three otherwise idle warps
+    // of the producer warpgroup, straight from the caller's column-major B
+    // (in L2 after first use), a few stages ahead; they transpose it in
+    // registers and store it as rows, so no packing pass over B runs before
+    // the launch and B is not part of the bulk copy.  The rows are BROWS
+    // elements apart; with one column warp (WK == 1) the 16-byte groups of
+    // row j sit XOR-swizzled by (j & 3), which spreads the loaders' 16-byte
+    // stores over the banks while every consumer address stays a
+    // compile-time offset.
+    static constexpr bool BLOAD = BT_ && !BRES_;
+    static constexpr bool BSWZ = BLOAD && WK_ == 1;
+    static constexpr int BROWS = BSWZ ? (KC_ <= 16 ? 16 : 32) : KC_;
     // Row blocks are never split between blocks (one group = one row block,
     // no partial sums): always with resident B, optionally with streamed B
     // (the TSM2L schedule for B too large to keep on chip).
@@ -61,16 +73,23 @@ struct Cfg {
     static constexpr int CC = cmin(KC, 4);   // C columns per cross-warp reduction round
     static constexpr int CQ = cmin(KCW, TSM2_CQ);  // C columns per group of the inner loop
     static constexpr int A_STAGE = BM * BNS;                 // elements
-    static constexpr int B_STAGE = BRES ? 0 : BNS * KC;      // elements
+    static constexpr int B_STAGE = (BRES || BLOAD) ? 0 : BNS * KC;  // elements copied with A (column-major)
+    static constexpr int BROW_STAGE = BLOAD ? BNS * BROWS : 0;       // elements stored by the loaders (rows)
     static constexpr int RED = WC > 1 ? WC * CC * BM : (SEPI ? WK * CC * BM : 0);  // elements
     static constexpr int BRES_ELEMS = BRES ? KC * NRES : 0;  // elements
     static constexpr uint32_t TX_BYTES = (uint32_t)((A_STAGE + B_STAGE) * sizeof(T));
     static constexpr size_t OFF_A = 0;
     static constexpr size_t OFF_B = OFF_A + (size_t)STAGES * A_STAGE * sizeof(T);
-    static constexpr size_t OFF_BRES = OFF_B + (size_t)STAGES * B_STAGE * sizeof(T);
+    static constexpr size_t OFF_BROW = OFF_B + (size_t)STAGES * B_STAGE * sizeof(T);
+    static constexpr size_t OFF_BRES = OFF_BROW + (size_t)STAGES * BROW_STAGE * sizeof(T);
     static constexpr size_t OFF_RED = OFF_BRES + (size_t)BRES_ELEMS * sizeof(T);
     static constexpr size_t OFF_BAR = align_up(OFF_RED + (size_t)RED * sizeof(T), 16);
-    static constexpr size_t OFF_FLAGS = OFF_BAR + 2 * STAGES * sizeof(uint64_t);
+    // full and empty barriers, STAGES each
+    static constexpr int NBAR = 2;
+    // Arrivals that complete a stage: the producer lane's (with the copy's
+    // bytes) and, with loaded B, one loader warp's.
+    static constexpr int FULL_ARRIVALS = BLOAD ? 2 : 1;
+    static constexpr size_t OFF_FLAGS = OFF_BAR + NBAR * STAGES * sizeof(uint64_t);
     static constexpr size_t SMEM = OFF_FLAGS + 32 + 128;  // + slack for 128-byte alignment
 
     static_assert(BT || JW % JV == 0, "a warp's columns must be whole B vectors");
@@ -86,7 +105,63 @@ struct Cfg {
                   "staged epilogue: whole row blocks, column rounds of CC, whole 16-byte vectors per thread");
     static_assert(SMEM <= 227 * 1024, "shared memory per block");
     static_assert(!BT || (sizeof(T) == 4 && KCW % 4 == 0), "row-major B: binary32, whole 16-byte column groups");
+    static_assert(!BSWZ || (JW % 4 == 0 && KC <= BROWS), "swizzle key j & 3 known per unrolled inner index");
+    static_assert(!BLOAD || BNS % 4 == 0, "loaded B: whole 4 x 4 blocks");
+    // A loader warp takes every third stage; with at least three stages the
+    // empty-barrier parity it waits on cannot alias an older phase.
+    static_assert(!BLOAD || STAGES >= 3, "loaded B needs three stages or more");
 };
+
+// Physical 16-byte group of logical group g (columns 4g .. 4g+3) in row j
+// of a loaded B tile.
+template <class K>
+__device__ __forceinline__ int bgroup(int j, int g) {
+    return K::BSWZ ? (g ^ (j & 3)) : g;
+}
+
+// One loader warp fills the B rows of a stage: rows j0 .. j0+BNS-1 of B
+// (n x k, column-major, ldb; 16-byte aligned with ldb a multiple of 4),
+// columns 0 .. KC-1, zero past n and k, as rows of BROWS elements: (j, c) at
+// brow[(j-j0)*BROWS + 4*bgroup<K>(j-j0, c/4) + c%4].  Block u (a lane's, in
+// steps of 32) covers rows 4(u/NG) .. +3 and columns 4(u%NG) .. +3: four
+// 16-byte loads down its columns, a register transpose, four 16-byte row
+// stores.
+template <class K>
+__device__ __forceinline__ void load_b_stage(const float *__restrict__ B, int64_t ldb, int64_t n, int k, int64_t j0,
+                                             float *brow, int lane) {
+    constexpr int NG = K::KC / 4;
+    constexpr int NBLK = (K::BNS / 4) * NG;
+#pragma unroll 1
+    for (int u = lane; u < NBLK; u += 32) {
+        const int q = u / NG, cg = u - (u / NG) * NG;
+        const int64_t jr = j0 + 4 * q;  // first row of the block
+        float4 v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int c = 4 * cg + i;
+            const float *col = B + jr + (int64_t)c * ldb;
+            if (c >= k) {
+                v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else if (jr + 3 < n) {
+                v[i] = __ldg(reinterpret_cast<const float4 *>(col));
+            } else {
+                v[i].x = jr + 0 < n ? __ldg(col + 0) : 0.f;
+                v[i].y = jr + 1 < n ? __ldg(col + 1) : 0.f;
+                v[i].z = jr + 2 < n ? __ldg(col + 2) : 0.f;
+                v[i].w = jr + 3 < n ? __ldg(col + 3) : 0.f;
+            }
+        }
+        const int j = 4 * q;
+        float *row = brow + j * K::BROWS;
+        *reinterpret_cast<float4 *>(row + 4 * bgroup<K>(j + 0, cg)) = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+        row += K::BROWS;
+        *reinterpret_cast<float4 *>(row + 4 * bgroup<K>(j + 1, cg)) = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
+        row += K::BROWS;
+        *reinterpret_cast<float4 *>(row + 4 * bgroup<K>(j + 2, cg)) = make_float4(v[0].z, v[1].z, v[2].z, v[3].z);
+        row += K::BROWS;
+        *reinterpret_cast<float4 *>(row + 4 * bgroup<K>(j + 3, cg)) = make_float4(v[0].w, v[1].w, v[2].w, v[3].w);
+    }
+}
 
 // One pipeline stage of one consumer warp (Alg. 2's inner update, with the
 // warp's share of the stage): for j over the warp's JW inner indices,
@@ -123,10 +198,13 @@ __device__ __forceinline__ void consume_stage(const typename K::T *a_st, const t
                 a[v * 4 + 2] = x.z;
                 a[v * 4 + 3] = x.w;
             }
-            const T *brow = b_st + j * K::KC + kbase;
+            const T *brow = b_st + j * K::BROWS + kbase;
 #pragma unroll
             for (int c0 = 0; c0 < K::KCW; c0 += 4) {
-                const float4 bq = *reinterpret_cast<const float4 *>(brow + c0);
+                // BSWZ: kbase = 0 and j & 3 = jj & 3 (JW % 4 == 0), so the
+                // swizzled group offset is a constant.
+                const int goff = K::BSWZ ? 4 * ((c0 >> 2) ^ (jj & 3)) : c0;
+                const float4 bq = *reinterpret_cast<const float4 *>(brow + goff);
                 const float2 b01 = make_float2(bq.x, bq.y);
                 const float2 b23 = make_float2(bq.z, bq.w);
 #pragma unroll

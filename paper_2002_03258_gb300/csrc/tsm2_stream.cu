@@ -9,8 +9,11 @@
 //    rows of C and keeps all KC accumulators of each row in registers; every
 //    element of A that reaches the lane is multiplied into all KC of them.
 //  * B staged on chip and read by broadcast (Algorithm 3, Sec. 3.1.3-3.1.4):
-//    the rows of B that pair with the current A tile sit in shared memory in
-//    column order; all lanes of a warp read the same 16 bytes at once.
+//    the rows of B that pair with the current A tile arrive in shared memory
+//    with it, in column order; all lanes of a warp read the same 16 bytes at
+//    once.  Configurations that read B row-major (two column pairs per
+//    16-byte load) have the three otherwise idle producer warps load each
+//    stage's B rows from global memory and store them transposed.
 //  * Prefetching (Algorithm 4, Sec. 3.1.5) becomes a STAGES-deep ring of
 //    shared-memory buffers filled by the tensor-memory accelerator: one
 //    producer lane issues 2-D bulk tensor copies of A tiles (BM rows x BNS
@@ -76,6 +79,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     T *sB = reinterpret_cast<T *>(smem + K::OFF_B);
     T *sBres = reinterpret_cast<T *>(smem + K::OFF_BRES);
     T *sRed = reinterpret_cast<T *>(smem + K::OFF_RED);
+    T *sBrow = reinterpret_cast<T *>(smem + K::OFF_BROW);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + K::OFF_BAR);
     uint64_t *empty = full + K::STAGES;
     volatile int *flags = reinterpret_cast<volatile int *>(smem + K::OFF_FLAGS);  // [0] abort, [1] last
@@ -99,7 +103,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             p.trace[4 * g + 3] = (unsigned long long)(u_end - u_begin);
         }
         for (int s = 0; s < K::STAGES; ++s) {
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], K::FULL_ARRIVALS);
             mbar_init(&empty[s], K::NW);
         }
         flags[0] = 0;
@@ -137,10 +141,9 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 #pragma unroll
                 for (int q = 0; q < K::NBOX; ++q)
                     tma_load_2d_hint(dstA + q * K::BOXM * K::BNS, &mapA, x0 + q * K::BOXM, y0, &full[s], policy);
-                // Row-major configurations read B from its packed transpose
-                // (KC x n, inner coordinate 0: aligned).
-                if constexpr (!K::BRES)
-                    tma_load_2d(sB + (size_t)s * K::B_STAGE, &mapB, K::BT ? 0 : y0, K::BT ? y0 : 0, &full[s]);
+                // B rows of the stage, column-major (BNS x KC box of B),
+                // unless the loader warps bring them.
+                if constexpr (!K::BRES && !K::BLOAD) tma_load_2d(sB + (size_t)s * K::B_STAGE, &mapB, y0, 0, &full[s]);
                 issued |= 1u << s;
                 last_par = (last_par & ~(1u << s)) | (ph << s);
                 if (++s == K::STAGES) { s = 0; ph ^= 1u; }
@@ -149,6 +152,29 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             // Let every copy this block started land before the block can exit.
             for (int t = 0; t < K::STAGES; ++t)
                 if (issued & (1u << t)) (void)mbar_wait_bounded(&full[t], (last_par >> t) & 1u, 4000000000LL, nullptr);
+        } else if (K::BLOAD && warp >= 1) {
+            // Loader warps 1..3: B rows of every third stage, from global
+            // memory, as soon as the stage is free again.
+            const int nunits = (int)(u_end - u_begin);
+            for (int i = warp - 1; i < nunits; i += 3) {
+                const int s = i % K::STAGES;
+                const uint32_t ph = (uint32_t)(i / K::STAGES) & 1u;
+                bool ok = !flags[0] && mbar_wait_bounded(&empty[s], ph ^ 1u, p.wait_ns, flags);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) {
+                    if (lane == 0) {
+                        flags[0] = 1;
+                        atomicOr(p.status, kStatusTimeout);
+                    }
+                    break;
+                }
+                const int64_t u = u_begin + i;
+                const int64_t jc = u - (u / p.upr) * p.upr;
+                load_b_stage<K>(static_cast<const float *>(p.B), p.ldb, p.n, p.k, jc * K::BNS,
+                                reinterpret_cast<float *>(sBrow + (size_t)s * K::BROW_STAGE), lane);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[s]);
+            }
         }
         return;
     }
@@ -209,6 +235,9 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             if constexpr (K::BRES) {
                 b_st = resident_b_stage<K>(sBres, jc);
                 bstride = K::NRES;
+            } else if constexpr (K::BLOAD) {
+                b_st = sBrow + (size_t)s * K::BROW_STAGE;
+                bstride = K::BROWS;
             } else {
                 b_st = sB + (size_t)s * K::B_STAGE;
                 bstride = K::BNS;
@@ -516,7 +545,6 @@ StreamShape shape_of(const char *name) {
     s.BOXM = K::BOXM;
     s.gran_rows = K::WHOLE ? 0 : 1;
     s.b_resident = K::BRES;
-    s.b_rowmajor = K::BT && !K::BRES;
     s.n_max_resident = K::NRES;
     s.smem_bytes = (int)K::SMEM;
     s.threads = K::THREADS;
@@ -558,31 +586,6 @@ const Entry kEntries[] = {
 
 
 }  // namespace
-
-template <typename T>
-__global__ void bt_pack_kernel(int64_t n, int k, const T *__restrict__ B, int64_t ldb, int kc, T *__restrict__ Bt) {
-    const int64_t total = n * kc;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = t / kc;
-        const int c = (int)(t - j * kc);
-        Bt[t] = c < k ? B[j + (int64_t)c * ldb] : T(0);
-    }
-}
-
-cudaError_t bt_pack_launch(int elem, int64_t n, int k, const void *B, int64_t ldb, int kc, void *Bt,
-                           cudaStream_t stream) {
-    const int64_t total = n * kc;
-    const int threads = 256;
-    const int64_t want = (total + threads - 1) / threads;
-    const int blocks = (int)(want < 1024 ? (want > 0 ? want : 1) : 1024);
-    if (elem == 8)
-        bt_pack_kernel<double><<<blocks, threads, 0, stream>>>(n, k, static_cast<const double *>(B), ldb, kc,
-                                                              static_cast<double *>(Bt));
-    else
-        bt_pack_kernel<float><<<blocks, threads, 0, stream>>>(n, k, static_cast<const float *>(B), ldb, kc,
-                                                             static_cast<float *>(Bt));
-    return cudaGetLastError();
-}
 
 const StreamShape *stream_shape(int elem, char op, int kc) {
     for (const Entry &en : kEntries)

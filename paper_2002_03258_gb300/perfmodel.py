@@ -6,10 +6,14 @@ at a time (``tile_size_C``), t3 the number of A elements fetched at a time
 (``tile_size_A``), ``bytes`` the element size.  Peak performance is in
 GFLOP/s and bandwidth in GB/s, as in the paper's platform table.
 
-Only the compute/memory classifier (``t2_threshold``) feeds the library: it
-decides whether a configuration is reported against the HBM roof or the ALU
-roof.  The occupancy and Little's-law estimates are kept for the report and as
-the seed of the tile search.
+Two parts feed the library's batched tuner (``autotune.seed_candidate``):
+the Little's-law estimate of bytes in flight per SM picks the seed tile
+variant (the pipeline must keep that much of A in flight), and the
+compute/memory classifier ``t2_threshold`` decides whether padding C columns
+up to a wider class costs time in the model.  The occupancy estimate
+(``max_occupancy``, ``util_mem``) is the paper's formula for thread-per-row
+kernels and is kept for reference; the library's persistent kernels run one
+block per SM by construction.
 """
 from __future__ import annotations
 

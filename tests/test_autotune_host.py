@@ -76,3 +76,48 @@ def test_concurrent_writers_never_leave_a_partial_file(tmp_path):
         final = json.load(f)
     assert final and all(isinstance(v, dict) and "ms" in v for v in final.values())
     assert not [f for f in os.listdir(tmp_path) if f != "tune.json"]
+
+
+from paper_2002_03258_gb300 import perfmodel  # noqa: E402
+from paper_2002_03258_gb300.autotune import (  # noqa: E402
+    MERGE_L, MERGE_R, candidates, in_flight_bytes, seed_candidate, stage_bytes)
+
+INFOS = [  # the compiled variants' parameters (tsm2_batch_v*.cu)
+    {"variant": 0, "stages": 5, "rows_per_lane": 8, "inner_per_warp": 4},
+    {"variant": 1, "stages": 4, "rows_per_lane": 8, "inner_per_warp": 4},
+    {"variant": 2, "stages": 5, "rows_per_lane": 4, "inner_per_warp": 4},
+    {"variant": 3, "stages": 5, "rows_per_lane": 4, "inner_per_warp": 8},
+]
+GB300 = perfmodel.Gpu("GB300", 79500.0, 6785.0, sms=152, clock_ghz=2.07)
+
+
+def test_stage_and_in_flight_bytes():
+    assert stage_bytes(INFOS[0]) == 256 * 32 * 4      # 256 rows x 32 inner columns, binary32
+    assert stage_bytes(INFOS[2]) == 128 * 32 * 4
+    assert stage_bytes(INFOS[3]) == 128 * 64 * 4
+    assert in_flight_bytes(INFOS[0]) == 4 * 32768
+    assert in_flight_bytes(INFOS[1]) == 3 * 32768
+
+
+def test_seed_follows_the_model():
+    # Little's law on GB300: ~21.6 KB per SM at 1000 cycles; every variant
+    # covers it, so the most rows per lane (then stages) wins: variant 0.
+    need = perfmodel.bytes_in_flight_per_sm(6785.0, 152, 2.07, 1000.0)
+    assert 20000 < need < 23000
+    assert seed_candidate(INFOS, GB300) == (0, MERGE_R | MERGE_L, "single")
+    # a latency so long that only the deepest rings qualify
+    deep = seed_candidate(INFOS, GB300, latency_cycles=4 * 2.07 * 152 * 98304 / 6785.0 / 4)
+    assert deep[0] in (0, 2, 3)
+    # nothing qualifies: the largest in-flight volume
+    assert seed_candidate(INFOS, GB300, latency_cycles=1e9)[0] == 0
+    # a GPU whose t2 threshold is below 32 columns: no merging (padding costs)
+    slow = perfmodel.Gpu("x", 1000.0, 6785.0, sms=152, clock_ghz=2.07)
+    assert seed_candidate(INFOS, slow)[1] == 0
+
+
+def test_candidates_cover_the_space_seed_first():
+    c = candidates(4, seed=(2, 0, "serial"))
+    assert c[0] == (2, 0, "serial")
+    assert len(c) == 4 * 2 * 2 and len(set(c)) == len(c)
+    assert {v for v, _, _ in c} == {0, 1, 2, 3}
+    assert {m for _, _, m in c} == {"single", "serial"}

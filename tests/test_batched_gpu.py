@@ -1,5 +1,6 @@
 """Batched plans (tsm2_batch_plan_*): every problem of an uneven batch against
-the CPU oracle, for every tile choice, grid share and launch mode."""
+the CPU oracle, for every tile variant, class set, grid and launch mode (one
+persistent launch, one launch per class, classes concurrently)."""
 import numpy as np
 import pytest
 
@@ -44,36 +45,83 @@ def check_all(items):
         assert_parity(got, it["A"], it["B"], np.float32)
 
 
-@pytest.mark.parametrize("flags", [0, 1, 2, 4, 7])
-def test_batch_plan_parity(flags):
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("merge", [False, True])
+def test_batch_plan_parity(variant, merge):
     import paper_2002_03258_gb300 as pkg
     import paper_2002_03258_gb300.batched as bt
     items = make_batch()
+    flags = bt.variant_flag(variant) | ((bt.MERGE_R | bt.MERGE_L) if merge else 0)
     plan = bt.BatchPlan([it["p"] for it in items], flags)
+    ncls = len(plan.classes())
+    assert plan.num_launches() == 1  # default: the whole batch in one persistent launch
+    assert all(c["name"].startswith(f"v{variant}_") for c in plan.classes())
+    if merge:
+        assert {c["name"].split("_kc")[1] for c in plan.classes()} <= {"16", "32"}
     plan.execute(0)
     assert pkg.tsm2_get_device_status(0) == 0
     check_all(items)
     first = [it["tC"].clone() for it in items]
-    # same plan as a CUDA graph, and with other SM shares: same results
+    # same plan as a CUDA graph: same bits (same grid, same split points)
     for it in items:
         it["tC"].fill_(float("nan"))
     plan.graph_launch(0)
     torch.cuda.synchronize()
     for a, it in zip(first, items):
         assert torch.equal(torch.nan_to_num(a, 7.0), torch.nan_to_num(it["tC"], 7.0))
-    ncls = len(plan.classes())
-    for grids in ([1] * ncls, [3] * ncls, [37] * ncls):
-        plan.set_grids(grids)
+    # other grids of the single launch, then the per-class modes (other split
+    # points: parity, not bits)
+    for g in (1, 37):
+        plan.set_single_grid(g)
+        for it in items:
+            it["tC"].fill_(float("nan"))
         plan.graph_launch(0)
         assert pkg.tsm2_get_device_status(0) == 0
         check_all(items)
-    # classes one after another on all SMs (other split points: parity, not bits)
-    plan.set_serial(True)
+    plan.set_mode("concurrent")
+    assert plan.num_launches() == ncls
+    for grids in ([1] * ncls, [3] * ncls, [37] * ncls):
+        plan.set_grids(grids)
+        for it in items:
+            it["tC"].fill_(float("nan"))
+        plan.graph_launch(0)
+        assert pkg.tsm2_get_device_status(0) == 0
+        check_all(items)
+    plan.set_mode("serial")
+    assert plan.num_launches() == ncls
     for it in items:
         it["tC"].fill_(float("nan"))
     plan.graph_launch(0)
     assert pkg.tsm2_get_device_status(0) == 0
     check_all(items)
+    for c in range(ncls):  # one class alone touches only its own problems' C
+        plan.execute_class(c, 0)
+    assert pkg.tsm2_get_device_status(0) == 0
+    check_all(items)
+    plan.close()
+
+
+def test_variant_info_and_bad_variant():
+    import paper_2002_03258_gb300 as pkg
+    import paper_2002_03258_gb300.batched as bt
+    n = bt.num_variants()
+    assert n == 4
+    infos = [bt.variant_info(v) for v in range(n)]
+    assert {i["stages"] for i in infos} >= {4, 5}
+    assert {i["rows_per_lane"] for i in infos} >= {4, 8}
+    assert {i["inner_per_warp"] for i in infos} >= {4, 8}
+    with pytest.raises(pkg.TSM2Error) as e:
+        bt.variant_info(n)
+    assert e.value.status == pkg.ERR_INVALID_VALUE
+    items = make_batch(seed=9)[:3]
+    with pytest.raises(pkg.TSM2Error) as e:
+        bt.BatchPlan([it["p"] for it in items], bt.variant_flag(n))
+    assert e.value.status == pkg.ERR_INVALID_VALUE
+    plan = bt.BatchPlan([it["p"] for it in items], 0)
+    with pytest.raises(pkg.TSM2Error):
+        plan.set_mode(7)
+    with pytest.raises(pkg.TSM2Error):
+        plan.set_single_grid(0)
     plan.close()
 
 
@@ -98,19 +146,24 @@ def test_autotuner_picks_a_valid_plan(tmp_path):
     from paper_2002_03258_gb300.autotune import autotune
     items = make_batch(seed=5)
     plan, rec = autotune([it["p"] for it in items], reps=2, cache_path=str(tmp_path / "tune.json"))
-    assert rec["ms"] > 0 and len(rec["trials"]) == 12
+    assert rec["ms"] > 0 and len(rec["trials"]) == 16
+    assert rec["trials"][0]["seed"] and rec["seed"]["rank"] >= 1
+    assert {t["variant"] for t in rec["trials"]} == {0, 1, 2, 3}
+    assert {(t["stages"], t["rows_per_lane"], t["inner_per_warp"]) for t in rec["trials"]} >= {(5, 8, 4), (4, 8, 4)}
     for it in items:
         it["tC"].fill_(float("nan"))
     plan.graph_launch(0)
     check_all(items)
     plan2, rec2 = autotune([it["p"] for it in items], cache_path=str(tmp_path / "tune.json"))
-    assert rec2.get("cached") and rec2["flags"] == rec["flags"]
+    assert rec2.get("cached") and (rec2["flags"], rec2["variant"], rec2["mode"]) == (rec["flags"], rec["variant"],
+                                                                                  rec["mode"])
     plan.close()
     plan2.close()
 
 
-@pytest.mark.parametrize("flags,serial", [(1, True), (0, False)])
-def test_batch_fullsize_workload_sampled(flags, serial):
+@pytest.mark.parametrize("variant,merge,mode,pitch", [(0, False, "single", 512), (3, True, "serial", 16),
+                                                      (1, False, "single", 16)])
+def test_batch_fullsize_workload_sampled(variant, merge, mode, pitch):
     """The benchmark's 512-problem workload (256 TSM2R n^2 x k, n in [512,
     8192]; 256 TSM2L, m in [2^14, 2^20], n = k in 4..32; about 43 GB of A and
     C), inputs generated on the device exactly as the benchmark makes them,
@@ -122,9 +175,10 @@ def test_batch_fullsize_workload_sampled(flags, serial):
     lib = pkg.lib()
     shapes = ti.batch_shapes(0)
     probs, bufs = [], []
+    pe = pitch // 4
     for idx, (op, m, n, k) in enumerate(shapes):
-        lda = (m + 3) // 4 * 4
-        ldb = (n + 3) // 4 * 4
+        lda = (m + pe - 1) // pe * pe
+        ldb = (n + pe - 1) // pe * pe
         tA = torch.empty((n, lda), dtype=torch.float32, device="cuda")
         tB = torch.empty((k, ldb), dtype=torch.float32, device="cuda")
         tC = torch.full((k, lda), float("nan"), dtype=torch.float32, device="cuda")
@@ -132,8 +186,8 @@ def test_batch_fullsize_workload_sampled(flags, serial):
         assert lib.tsm2_fill_uniform_s(n, k, idx, ti.MID_B, tB.data_ptr(), ldb, 0) == 0
         bufs.append((tA, tB, tC))
         probs.append(bt.problem(op, m, n, k, tA.data_ptr(), lda, tB.data_ptr(), ldb, tC.data_ptr(), lda))
-    plan = bt.BatchPlan(probs, flags)
-    plan.set_serial(serial)
+    plan = bt.BatchPlan(probs, bt.variant_flag(variant) | ((bt.MERGE_R | bt.MERGE_L) if merge else 0))
+    plan.set_mode(mode)
     plan.graph_launch(0)
     assert pkg.tsm2_get_device_status(0) == 0
     # every fourth problem of the (shuffled) batch, 10 random rows plus the

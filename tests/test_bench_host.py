@@ -14,17 +14,18 @@ def test_algorithmic_bytes():
 
 
 def test_launches_per_call():
-    # TSM2R: one launch per 16-column chunk, plus the B packing kernel before
-    # chunks of 9..16 columns; TSM2L: 32-column chunks, packing only for n > 64.
+    # One launch per column chunk: 16 columns for TSM2R, 32 for TSM2L; B is
+    # transposed on chip, so no packing launches.
     assert bench.launches_per_call("r", 30720, 2) == 1
     assert bench.launches_per_call("r", 30720, 8) == 1
-    assert bench.launches_per_call("r", 30720, 9) == 2
-    assert bench.launches_per_call("r", 30720, 16) == 2
-    assert bench.launches_per_call("r", 30720, 20) == 3   # 16 (+ pack) + 4
-    assert bench.launches_per_call("r", 30720, 33) == 5   # 16 + 16 (+ packs) + 1
+    assert bench.launches_per_call("r", 30720, 9) == 1
+    assert bench.launches_per_call("r", 30720, 16) == 1
+    assert bench.launches_per_call("r", 30720, 20) == 2   # 16 + 4
+    assert bench.launches_per_call("r", 30720, 33) == 3   # 16 + 16 + 1
     assert bench.launches_per_call("l", 32, 32) == 1      # (op, inner n, k)
-    assert bench.launches_per_call("l", 100, 100) == 8    # 32, 32, 32, 4, each with a pack
+    assert bench.launches_per_call("l", 100, 100) == 4    # 32, 32, 32, 4
     assert bench.launches_per_call("l", 64, 40) == 2
+    assert bench.launches_per_call("r", 100, 0) == 0
 
 
 def test_sweep_cases():
