@@ -221,9 +221,8 @@ tsm2_status tsm2l_d_host(int64_t m, int64_t n, int64_t k, const double *A, int64
  * device memory is wholly owned by another allocator (a framework's caching
  * pool that has reserved the free memory), or a latency-bound loop that
  * cannot pay for cudaMalloc and its implicit synchronisation.
- *  - Scratch: partial sums of row blocks split between thread blocks, their
- *    arrival counters and (column chunks 9..16 wide, KC = 12 or 16 columns)
- *    a packed n x KC copy of B live in a fixed 16 MiB array in device memory.
+ *  - Scratch: partial sums of row blocks split between thread blocks and
+ *    their arrival counters live in a fixed 16 MiB array in device memory.
  *    The array belongs to the library's device code: it is reserved, with the
  *    library's status word, when that code is first loaded on a device, which
  *    is the first call of any tsm2 entry point there (CUDA loads modules
@@ -232,10 +231,10 @@ tsm2_status tsm2l_d_host(int64_t m, int64_t n, int64_t k, const double *A, int64
  *    allocator reserves all free device memory should make one tsm2 call on
  *    each device first, or that first call can fail for lack of memory.
  *  - Limit: those must fit the array: m up to about 222,000 rows when a
- *    column chunk is 9..16 wide and n is small, fewer as n grows (4 KC bytes
- *    of packed B per inner index: 48 for KC = 12, 64 for KC = 16), more for
- *    narrower k (the sizes are in the error message).  Larger problems return
- *    TSM2_ERR_UNSUPPORTED before anything is launched.
+ *    column chunk is 13..16 wide (KC = 16; the partial-sum slots grow with m,
+ *    not with n), more for narrower chunks (the sizes are in the error
+ *    message).  Larger problems return TSM2_ERR_UNSUPPORTED before anything
+ *    is launched.
  *  - Set-up: the first call on each device looks up the array's device
  *    address (cudaGetSymbolAddress) with that device current; make that first
  *    call before any stream capture.
