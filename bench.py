@@ -911,7 +911,8 @@ def run_host_case(args):
 def run_batch_case(args):
     """One tile class of the batched workload: the first `count` problems of
     the 512-problem batch whose op is `op` and whose k chunk uses the C-column
-    width `kc`, as one plan (flags), executed like the batched leg (for the
+    width `kc` (op "x": the first `count` problems, any class), as one plan
+    (flags; default mode, one launch), executed like the batched leg (for the
     ncu captures of the batched kernel)."""
     import torch
 
@@ -929,7 +930,10 @@ def run_batch_case(args):
     lib = pkg.lib()
     probs, keep, total = [], [], 0
     for idx, (o, m, n, k) in enumerate(ti.batch_shapes(0)):
-        if o != op or next(w for w in widths if w >= min(k, 32 if o == "l" else 16)) != kc or len(probs) >= count:
+        if len(probs) >= count:
+            break
+        # op "x", kc 0: the first `count` problems of the batch, any class
+        if op != "x" and (o != op or next(w for w in widths if w >= min(k, 32 if o == "l" else 16)) != kc):
             continue
         lda, ldb = (m + pe - 1) // pe * pe, (n + pe - 1) // pe * pe
         tA = torch.empty((n, lda), dtype=torch.float32, device="cuda")
@@ -955,7 +959,8 @@ def run_batch_case(args):
             ts.append(e0.elapsed_time(e1))
     pkg.check(pkg.tsm2_get_device_status(0))
     ms = statistics.median(ts)
-    print(json.dumps({"batch_case": args.batch_case, "problems": len(probs), "classes": [c["name"] for c in plan.classes()],
+    print(json.dumps({"batch_case": args.batch_case, "problems": len(probs), "launches": plan.num_launches(),
+                      "classes": [c["name"] for c in plan.classes()],
                       "ms": round(ms, 4), "gbs": round(total / (ms * 1e-3) / 1e9, 1), "algorithmic_bytes": total}),
           flush=True)
     plan.close()
