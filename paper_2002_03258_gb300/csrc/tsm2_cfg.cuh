@@ -330,11 +330,21 @@ static_assert(4 * 32 * kProducerRegs + 8 * 32 * kConsumerRegs <= 384 * 168, "reg
 #define TSM2_R16_JW 4
 #endif
 #ifndef TSM2_R16_STAGES
-#define TSM2_R16_STAGES 5
+#define TSM2_R16_STAGES 4
+#endif
+// Pipeline stages (measured on GB300, 30720^2 and 10240^2): four for 8..16
+// C columns (k = 16: 0.6048 -> 0.5987 ms, k = 8: 0.5731 -> 0.5669 ms at
+// 30720^2 against five; three is slower again), five for 2..4 columns.
+#ifndef TSM2_R_STAGES
+#define TSM2_R_STAGES 5
+#endif
+#ifndef TSM2_R8_STAGES
+#define TSM2_R8_STAGES 4
 #endif
 template <int KC>
 using R32 = Cfg<float, KC, (KC >= 16 ? TSM2_R16_NV : 2), 1, 8, 1, (KC >= 16 ? TSM2_R16_JW : 4),
-                (KC >= 16 ? TSM2_R16_STAGES : 5), false, 0, (KC >= 12), (KC >= 16 && TSM2_R16_NV == 3 ? 128 : 0)>;
+                (KC >= 16 ? TSM2_R16_STAGES : (KC >= 8 ? TSM2_R8_STAGES : TSM2_R_STAGES)), false, 0, (KC >= 12),
+                (KC >= 16 && TSM2_R16_NV == 3 ? 128 : 0)>;
 template <int KC> using R64 = Cfg<double, KC, 2, 1, 8, 1, 4, 5, false, 0>;
 // TSM2L: resident B row-major wherever a warp's C columns are whole groups of
 // four (the B load at block start transposes; no packed copy needed).
@@ -345,8 +355,11 @@ template <int KC> using R64 = Cfg<double, KC, 2, 1, 8, 1, 4, 5, false, 0>;
 //   binary32: R = 4, BM = 1024, BNS = 8.   binary64: R = 2, BM = 512, BNS = 8.
 //   KC = 32 splits the C columns over 2 x 4 warps (16 accumulated columns per
 //   lane, BM halves) to keep the accumulators in registers.
+#ifndef TSM2_L_STAGES
+#define TSM2_L_STAGES 5
+#endif
 template <int KC>
-using L32 = Cfg<float, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, 5, true, 64,
+using L32 = Cfg<float, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, TSM2_L_STAGES, true, 64,
                 (TSM2_L_BT != 0 && (KC / (KC >= 32 ? 2 : 1)) % 4 == 0)>;
 template <int KC> using L64 = Cfg<double, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, 5, true, 64>;
 // TSM2L schedule for tall A (binary32): R = 8 rows per lane, so every B value
@@ -364,25 +377,19 @@ struct WShape {
     int nv, wr, wk, jw, st;
     bool sepi;
 };
+#ifndef TSM2_W_STAGES
+#define TSM2_W_STAGES 5
+#endif
 constexpr WShape w32_shape(int kc) {
-    return kc >= 32   ? WShape{2, 4, 2, 8, 5, false}   // 16 columns per lane
-           : kc >= 24 ? WShape{2, 4, 2, 8, 5, false}   // 12 columns per lane
-           : kc >= 16 ? WShape{2, 8, 1, 4, 5, true}
-                      : WShape{2, 8, 1, 4, 5, false};
+    return kc >= 32   ? WShape{2, 4, 2, 8, TSM2_W_STAGES, false}   // 16 columns per lane
+           : kc >= 24 ? WShape{2, 4, 2, 8, TSM2_W_STAGES, false}   // 12 columns per lane
+           : kc >= 16 ? WShape{2, 8, 1, 4, TSM2_W_STAGES, true}
+                      : WShape{2, 8, 1, 4, TSM2_W_STAGES, false};
 }
 template <int KC>
 using W32 = Cfg<float, KC, w32_shape(KC).nv, w32_shape(KC).wr, 1, w32_shape(KC).wk, w32_shape(KC).jw,
                 w32_shape(KC).st, true, 64, (TSM2_L_BT != 0 && (KC / w32_shape(KC).wk) % 4 == 0), 0, false,
                 w32_shape(KC).sepi>;
-// The batched kernel writes C straight from registers: 16 C columns per lane
-// for KC = 32 (as the single-problem kernel), 8-12 below.
-constexpr WShape w32n_shape(int kc) {
-    return kc >= 16 ? WShape{2, 4, 2, 8, 5, false} : WShape{2, 8, 1, 4, 5, false};
-}
-template <int KC>
-using W32N = Cfg<float, KC, w32n_shape(KC).nv, w32n_shape(KC).wr, 1, w32n_shape(KC).wk, w32n_shape(KC).jw,
-                 w32n_shape(KC).st, true, 64, (TSM2_L_BT != 0 && (KC / w32n_shape(KC).wk) % 4 == 0)>;
-
 // TSM2L with B staged instead of resident (Alg. 6's setting, Sec. 3.2.2: B
 // too large to stay on chip, here n > 64): B rows arrive with each A stage,
 // but every block still owns whole row blocks and keeps their C columns in
