@@ -104,7 +104,11 @@ def test_seed_follows_the_model():
     # covers it, so the most rows per lane (then stages) wins: variant 0.
     need = perfmodel.bytes_in_flight_per_sm(6785.0, 152, 2.07, 1000.0)
     assert 20000 < need < 23000
-    assert seed_candidate(INFOS, GB300) == (0, MERGE_R | MERGE_L, "single")
+    # t2 threshold at the sustained FMA rate: 79.5 TF x 0.65 / 6.785 TB/s x 4
+    # = 30.5 columns < 32, so the seed keeps the classes apart; at the full
+    # peak (the paper's assumption) it would merge them.
+    assert seed_candidate(INFOS, GB300) == (0, 0, "single")
+    assert seed_candidate(INFOS, GB300, fma_sustained=1.0) == (0, MERGE_R | MERGE_L, "single")
     # a latency so long that only the deepest rings qualify
     deep = seed_candidate(INFOS, GB300, latency_cycles=4 * 2.07 * 152 * 98304 / 6785.0 / 4)
     assert deep[0] in (0, 2, 3)
