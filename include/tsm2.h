@@ -252,7 +252,7 @@ tsm2_status tsm2r_s_noalloc(int64_t m, int64_t n, int64_t k,
  *
  * Many TSM2R / TSM2L problems of different shapes executed as one unit.  The
  * problems are grouped into tile classes (schedule and C-column width KC:
- * TSM2R with 8 or 16 columns, TSM2L with 8, 16, 24 or 32; each column chunk
+ * TSM2R with 8, 12 or 16 columns, TSM2L with 8, 16, 24 or 32; each column chunk
  * goes to the narrowest class that holds it).  In every class the work units
  * of all its problems are numbered end to end and every block of a persistent
  * grid takes an equal, contiguous share, crossing problem boundaries

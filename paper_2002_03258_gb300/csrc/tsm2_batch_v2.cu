@@ -20,7 +20,7 @@ using VW = Cfg<float, KC, kNV, (KC >= 16 ? 4 : 8), 1, (KC >= 16 ? 2 : 1), (KC >=
                ((KC / (KC >= 16 ? 2 : 1)) % 4 == 0)>;
 
 const BatchClass kSlots[] = {
-    class_of<VR<8>>('r', "v2_r_kc8"),   class_of<VR<16>>('r', "v2_r_kc16"),
+    class_of<VR<8>>('r', "v2_r_kc8"),   class_of<VR<12>>('r', "v2_r_kc12"), class_of<VR<16>>('r', "v2_r_kc16"),
     class_of<VW<8>>('w', "v2_l_kc8"),   class_of<VW<16>>('w', "v2_l_kc16"),
     class_of<VW<24>>('w', "v2_l_kc24"), class_of<VW<32>>('w', "v2_l_kc32"),
 };
@@ -29,9 +29,9 @@ const BatchClass kSlots[] = {
 
 const BatchMenu *batch_menu_v2() {
     static const BatchMenu menu = {
-        "stages 5, 4 rows per lane, 4 inner columns per warp", kStages, 4 * kNV, kJW, 6,
-        {&kSlots[0], &kSlots[1], &kSlots[2], &kSlots[3], &kSlots[4], &kSlots[5], nullptr, nullptr},
-        &launch_batch_kernel<kPregs, VR<8>, VR<16>, VW<8>, VW<16>, VW<24>, VW<32>>};
+        "stages 5, 4 rows per lane, 4 inner columns per warp", kStages, 4 * kNV, kJW, 7,
+        {&kSlots[0], &kSlots[1], &kSlots[2], &kSlots[3], &kSlots[4], &kSlots[5], &kSlots[6], nullptr},
+        &launch_batch_kernel<kPregs, VR<8>, VR<12>, VR<16>, VW<8>, VW<16>, VW<24>, VW<32>>};
     return &menu;
 }
 

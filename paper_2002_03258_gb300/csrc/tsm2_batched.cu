@@ -1,7 +1,7 @@
 // Tile variants of the batch kernel (tsm2_batch_kernel.cuh) and their menus.
 //
-// Each variant is one kernel holding six tile classes: TSM2R with 8 or 16 C
-// columns and TSM2L (whole row blocks, B resident) with 8, 16, 24 or 32.  A
+// Each variant is one kernel holding seven tile classes: TSM2R with 8, 12 or
+// 16 C columns and TSM2L (whole row blocks, B resident) with 8, 16, 24 or 32.  A
 // problem's column chunk goes to the narrowest class of its schedule that
 // holds it (or, with the merge flags, to the widest).  The variants differ in
 // the tile parameters the paper leaves to offline tuning (t1, t3 and tcf,
