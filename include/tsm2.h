@@ -41,7 +41,8 @@
  *    Faults during execution surface at the caller's next synchronisation,
  *    as for any CUDA kernel.  A pipeline wait that exceeds its time bound
  *    sets a device status word instead of hanging; tsm2_get_device_status()
- *    reports it as TSM2_ERR_TIMEOUT.
+ *    reports it as TSM2_ERR_TIMEOUT (and, in the debug build, a skipped
+ *    out-of-bounds access as TSM2_ERR_BOUNDS; see tsm2_debug_checks).
  *  - Alignment: any alignment is accepted.  16-byte aligned base pointers
  *    with leading dimensions whose byte size is a multiple of 16 select the
  *    bulk-copy (TMA) path; anything else selects a slower path that loads
@@ -75,7 +76,8 @@ typedef enum tsm2_status {
     TSM2_ERR_INVALID_VALUE = 1,
     TSM2_ERR_UNSUPPORTED = 2,
     TSM2_ERR_CUDA = 3,
-    TSM2_ERR_TIMEOUT = 4
+    TSM2_ERR_TIMEOUT = 4,
+    TSM2_ERR_BOUNDS = 5  /* debug builds only: an access outside its operand was skipped */
 } tsm2_status;
 
 /* TSM2R, binary64.  A is streamed from device memory once per group of up
@@ -361,6 +363,15 @@ tsm2_status tsm2_get_device_status(void *stream);
 /* Frees every workspace the library allocated (all devices).  Call with no
  * library work in flight.  The library stays usable; it reallocates lazily. */
 void tsm2_shutdown(void);
+
+/* 1 in the debug build of the library (libtsm2_debug.so, compiled with
+ * -DTSM2_DEBUG), 0 otherwise.  The debug build checks every hand-computed
+ * global address of the bulk-copy, batched and backward kernels against the
+ * extents of its operand (rows and columns of C and B, workspace slots,
+ * arrival counters) before the access; an access that would fall outside is
+ * skipped and recorded, and tsm2_get_device_status then returns
+ * TSM2_ERR_BOUNDS.  It stands in for a memory checker: nothing faults. */
+int tsm2_debug_checks(void);
 
 /* ---- Tuning and debugging knobs (process-wide, not thread-safe) ---------- */
 

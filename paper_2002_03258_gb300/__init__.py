@@ -18,13 +18,16 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libtsm2.so")
+# TSM2_DEBUG=1 selects the bounds-checking build (build(debug=True)).
+DEBUG = os.environ.get("TSM2_DEBUG", "0") not in ("", "0")
+LIB_PATH = os.path.join(_HERE, "_build", "libtsm2_debug.so" if DEBUG else "libtsm2.so")
 
 SUCCESS = 0
 ERR_INVALID_VALUE = 1
 ERR_UNSUPPORTED = 2
 ERR_CUDA = 3
 ERR_TIMEOUT = 4
+ERR_BOUNDS = 5
 
 _lock = threading.Lock()
 _lib = None
@@ -44,7 +47,9 @@ def _load():
         if _lib is None:
             if not os.path.exists(LIB_PATH):
                 raise RuntimeError(
-                    f"CUDA library not built ({LIB_PATH} missing); run `python -c \"import __graft_entry__ as g; g.build()\"`")
+                    f"CUDA library not built ({LIB_PATH} missing); run "
+                    + ("`python -m paper_2002_03258_gb300.build --debug`" if DEBUG else
+                       "`python -c \"import __graft_entry__ as g; g.build()\"`"))
             lib = ctypes.CDLL(LIB_PATH)
             i64, vp, u64 = ctypes.c_int64, ctypes.c_void_p, ctypes.c_uint64
             gemm_sig = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]
@@ -110,6 +115,8 @@ def _load():
                 f = getattr(lib, name)
                 f.argtypes = [i64, i64, u64, u64, vp, i64, vp]
                 f.restype = ctypes.c_int
+            lib.tsm2_debug_checks.argtypes = []
+            lib.tsm2_debug_checks.restype = ctypes.c_int
             lib.tsm2_fma_probe.argtypes = [ctypes.c_int, ctypes.c_int, i64, vp, vp]
             lib.tsm2_fma_probe.restype = ctypes.c_int
             for name in ("tsm2_fill_normal_ih_d", "tsm2_fill_normal_ih_s"):

@@ -3,6 +3,9 @@
 Each translation unit under ``csrc/`` is compiled in parallel, then linked
 into one shared library (static CUDA runtime; the driver entry point for
 tensor-map encoding is resolved at run time, so no libcuda link is needed).
+``build(debug=True)`` makes the bounds-checking variant
+``_build/libtsm2_debug.so`` (the same sources with ``-DTSM2_DEBUG``; objects
+in ``_build/debug/``), which the binding loads when ``TSM2_DEBUG=1``.
 """
 from __future__ import annotations
 
@@ -17,6 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtsm2.so")
+DEBUG_DIR = os.path.join(OUT_DIR, "debug")
+DEBUG_LIB = os.path.join(OUT_DIR, "libtsm2_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -39,15 +44,17 @@ def _deps_mtime():
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime() and not extra_flags:
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra_flags=None, debug: bool = False) -> str:
+    lib_path = DEBUG_LIB if debug else LIB
+    obj_dir = DEBUG_DIR if debug else OUT_DIR
+    os.makedirs(obj_dir, exist_ok=True)
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= _deps_mtime() and not extra_flags:
+        return lib_path
     cc = nvcc()
-    flags = NVCC_FLAGS + list(extra_flags or [])
+    flags = NVCC_FLAGS + (["-DTSM2_DEBUG"] if debug else []) + list(extra_flags or [])
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, *flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -59,13 +66,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     srcs = sources()
     with ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     r = subprocess.run([cc, "-shared", *ARCH, "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

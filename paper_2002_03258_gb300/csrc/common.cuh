@@ -11,6 +11,28 @@ namespace tsm2 {
 
 // Status bits written to the device status word.
 constexpr unsigned kStatusTimeout = 1u;
+constexpr unsigned kStatusBounds = 2u;  // debug builds: an access outside its operand was skipped
+
+// Debug builds (-DTSM2_DEBUG) check every hand-computed global address
+// against the extents of the operand it belongs to (rows and columns of C or
+// B, workspace slots, arrival counters) before the access.  dbg_in_bounds
+// returns `ok`; when it is false it records kStatusBounds in the status word
+// and the caller skips the access, so a wrong index shows up as a status
+// instead of a fault.  Release builds compile it to `true`.
+#ifdef TSM2_DEBUG
+constexpr bool kDebugChecks = true;
+#else
+constexpr bool kDebugChecks = false;
+#endif
+__device__ __forceinline__ bool dbg_in_bounds(bool ok, unsigned *status) {
+    if constexpr (kDebugChecks) {
+        if (!ok) {
+            atomicOr(status, kStatusBounds);
+            return false;
+        }
+    }
+    return true;
+}
 
 // 16-byte vector of T: float4 for binary32, double2 for binary64.
 template <typename T> struct Vec16;

@@ -146,6 +146,7 @@ struct ClassParams {
     int64_t ngroups;  // 0: the class has no work in this launch
     float *ws;        // partial-sum slots: (grid + row blocks) x KC x BM
     int *counters;    // one arrival counter per row block, zero between launches
+    int64_t nrb;      // row blocks of the class (counters; slots beyond the grid)
 };
 
 struct BatchKParams {

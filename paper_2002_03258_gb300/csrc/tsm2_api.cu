@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/tsm2.h): argument checking,
 // choice of kernel path and configuration, tensor-map encoding, workspace
 // management and the device status word.
+#include "common.cuh"
 #include "internal.h"
 #include "tsm2.h"
 
@@ -20,7 +21,7 @@
 namespace tsm2 {
 namespace {
 
-__device__ unsigned int g_status_word;  // per device; bit kStatusTimeout set by kernels
+__device__ unsigned int g_status_word;  // per device; bits kStatusTimeout, kStatusBounds set by kernels
 
 thread_local std::string t_last_error = "no error";
 thread_local const char *t_last_config = "none";
@@ -640,6 +641,7 @@ void class_params(const tsm2_batch_plan_s::Cls &c, ClassParams &cp) {
     cp.ngroups = c.ngroups;
     cp.counters = static_cast<int *>(c.d_ws);
     cp.ws = reinterpret_cast<float *>(static_cast<char *>(c.d_ws) + c.counter_bytes);
+    cp.nrb = c.nrb;
 }
 
 // One launch of the plan's batch kernel over the classes [lo, hi) (all
@@ -1157,8 +1159,14 @@ tsm2_status tsm2_get_device_status(void *stream) {
     }
     reset_plan_counters(dev);
     cudaDeviceSynchronize();
+    if (w & kStatusBounds)
+        return set_error(TSM2_ERR_BOUNDS,
+                         "debug build: a kernel computed an address outside its operand and skipped the access; the "
+                         "output of that call is undefined");
     return set_error(TSM2_ERR_TIMEOUT, "a pipeline wait exceeded its bound; the output of that call is undefined");
 }
+
+int tsm2_debug_checks(void) { return kDebugChecks ? 1 : 0; }
 
 void tsm2_shutdown(void) {
     int cur = 0;

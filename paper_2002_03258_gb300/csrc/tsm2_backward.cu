@@ -266,7 +266,8 @@ tsm2t_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
 #pragma unroll
                 for (int o0 = 0; o0 < K::NOUT; o0 += 32) {
                     const int o = o0 + lane;
-                    if (o < K::NOUT) __stcg(slot + cw * K::NOUT + o, mine[o0 >> 5]);
+                    if (o < K::NOUT && dbg_in_bounds(g + jc < G + p.nunits / p.nrb, p.status))
+                        __stcg(slot + cw * K::NOUT + o, mine[o0 >> 5]);
                 }
                 __threadfence();
                 named_bar_sync(1, 256);
@@ -275,7 +276,7 @@ tsm2t_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
                 const int64_t gB = owner_of_t(cu0 + p.nrb - 1, G, p.nunits);
                 if (threadIdx.x == 128) {
                     int last = 0;
-                    if (!flags[0]) {
+                    if (!flags[0] && dbg_in_bounds(jc < p.nunits / p.nrb, p.status)) {
                         const int old = atomicAdd(&p.counters[jc], 1);
                         last = (old == (int)(gB - gA));
                         if (last) p.counters[jc] = 0;
@@ -283,7 +284,7 @@ tsm2t_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
                     flags[1] = last;
                 }
                 named_bar_sync(1, 256);
-                if (flags[1]) {
+                if (flags[1] && dbg_in_bounds(gA >= 0 && gB + jc < G + p.nunits / p.nrb, p.status)) {
                     __threadfence();
                     for (int o0 = 0; o0 < K::NOUT; o0 += 32) {
                         const int o = o0 + lane;

@@ -78,6 +78,19 @@ struct StageMeta {
 };
 static_assert(sizeof(StageMeta) == 32, "stage record size");
 
+// Block g's share of a class: groups [g*NG/Gc, (g+1)*NG/Gc) with
+// Gc = min(grid, NG).  With more blocks than groups only the first NG blocks
+// take one group each, so every block between the first and last owner of a
+// split row block has written its partial sum (the fix-up adds them all).
+__device__ __forceinline__ bool class_share(const ClassParams &cp, int64_t &Gc, int64_t &gs, int64_t &ge) {
+    const int64_t G = gridDim.x, g = blockIdx.x;
+    Gc = G < cp.ngroups ? G : cp.ngroups;
+    if (g >= Gc) return false;
+    gs = g * cp.ngroups / Gc;
+    ge = (g + 1) * cp.ngroups / Gc;
+    return gs < ge;
+}
+
 __device__ __forceinline__ int find_problem(const ProbDesc *probs, int nprob, int64_t gidx) {
     int lo = 0, hi = nprob - 1;  // last problem with group_begin <= gidx
     while (lo < hi) {
@@ -145,9 +158,8 @@ __device__ __forceinline__ void produce_class(const ClassParams &cp, int cls, un
                                               uint64_t *empty, uint64_t *metab, volatile int *flags,
                                               const BatchKParams &p, Ring &ring, uint32_t &issued,
                                               uint32_t &last_par, bool &stop, uint64_t policy) {
-    const int64_t G = gridDim.x, g = blockIdx.x;
-    const int64_t gs = g * cp.ngroups / G, ge = (g + 1) * cp.ngroups / G;
-    if (stop || gs >= ge) return;
+    int64_t Gc, gs, ge;
+    if (stop || !class_share(cp, Gc, gs, ge)) return;
     Walk w;
     w.start(cp, gs);
     for (int64_t gg = gs; gg < ge && !stop; ++gg) {
@@ -185,9 +197,8 @@ __device__ __forceinline__ void produce_class(const ClassParams &cp, int cls, un
 
 // Stages a block runs in one class: whole groups of gran stages each.
 __device__ __forceinline__ int64_t class_units(const ClassParams &cp) {
-    const int64_t G = gridDim.x, g = blockIdx.x;
-    const int64_t gs = g * cp.ngroups / G, ge = (g + 1) * cp.ngroups / G;
-    if (gs >= ge) return 0;
+    int64_t Gc, gs, ge;
+    if (!class_share(cp, Gc, gs, ge)) return 0;
     int64_t units = 0;
     for (int pi = find_problem(cp.probs, cp.nprob, gs); pi < cp.nprob; ++pi) {
         const ProbDesc &d = cp.probs[pi];
@@ -201,9 +212,9 @@ __device__ __forceinline__ int64_t class_units(const ClassParams &cp) {
 }
 
 template <class K>
-__device__ __forceinline__ void load_if(bool hit, const StageMeta &m, float *brow, int lane) {
+__device__ __forceinline__ void load_if(bool hit, const StageMeta &m, float *brow, int lane, unsigned *status) {
     if constexpr (K::BLOAD)
-        if (hit) load_b_stage<K>(m.b, m.ldb, m.rows, m.k, 0, brow, lane);
+        if (hit) load_b_stage<K>(m.b, m.ldb, m.rows, m.k, 0, brow, lane, status);
 }
 
 // Loader warps 1..3 of the producer warpgroup: warp w takes every third stage
@@ -232,7 +243,7 @@ __device__ __forceinline__ void loader_warp(const BatchKParams &p, unsigned char
         if (m.b) {
             float *brow = reinterpret_cast<float *>(smem + LY::OFF_BROW + (size_t)s * LY::BROW_BYTES);
             int c = 0;
-            (load_if<Ks>(c++ == m.cls, m, brow, lane), ...);
+            (load_if<Ks>(c++ == m.cls, m, brow, lane, p.status), ...);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&full[s]);
@@ -250,9 +261,9 @@ __device__ __forceinline__ void consume_class(const ClassParams &cp, unsigned ch
                                               Ring &ring, bool &aborted) {
     using T = float;
     using vec_t = typename K::vec_t;
-    const int64_t G = gridDim.x, g = blockIdx.x;
-    const int64_t gs = g * cp.ngroups / G, ge = (g + 1) * cp.ngroups / G;
-    if (gs >= ge) return;
+    int64_t G, gs, ge;  // G: the blocks that share this class
+    if (!class_share(cp, G, gs, ge)) return;
+    const int64_t g = blockIdx.x;
     T *sBres = reinterpret_cast<T *>(smem + LY::OFF_BRES);
     T *sRed = reinterpret_cast<T *>(smem + LY::OFF_RED);
     const int warp = threadIdx.x >> 5;
@@ -359,7 +370,8 @@ __device__ __forceinline__ void consume_class(const ClassParams &cp, unsigned ch
                                     T tmp[K::V];
 #pragma unroll
                                     for (int e = 0; e < K::V; ++e) tmp[e] = acc[v * K::V + e][c];
-                                    *reinterpret_cast<vec_t *>(cw + row_of(v)) = K::VT::make(tmp);
+                                    if (dbg_in_bounds(row0 + row_of(v) + K::V - 1 < m && kbase + c < kk, p.status))
+                                        *reinterpret_cast<vec_t *>(cw + row_of(v)) = K::VT::make(tmp);
                                 }
                                 cw += ldc;
                             }
@@ -373,7 +385,8 @@ __device__ __forceinline__ void consume_class(const ClassParams &cp, unsigned ch
                                         T tmp[K::V];
 #pragma unroll
                                         for (int e = 0; e < K::V; ++e) tmp[e] = acc[v * K::V + e][c];
-                                        *reinterpret_cast<vec_t *>(cw + row_of(v)) = K::VT::make(tmp);
+                                        if (dbg_in_bounds(row0 + row_of(v) + K::V - 1 < m, p.status))
+                                            *reinterpret_cast<vec_t *>(cw + row_of(v)) = K::VT::make(tmp);
                                     }
                                 }
                                 cw += ldc;
@@ -418,7 +431,7 @@ __device__ __forceinline__ void consume_class(const ClassParams &cp, unsigned ch
                             const int c = c0 + cc;
                             if (whole) {
                                 if (!aborted && c < kk && row0 + row < m) C[row0 + row + (int64_t)c * ldc] = sum;
-                            } else {
+                            } else if (dbg_in_bounds(g + rbg < G + cp.nrb, p.status)) {
                                 __stcg(slot + c * K::BM + row, sum);
                             }
                         }
@@ -430,7 +443,7 @@ __device__ __forceinline__ void consume_class(const ClassParams &cp, unsigned ch
                         named_bar_sync(1, K::NT);
                         if (tid == 0) {
                             int lastp = 0;
-                            if (!flags[0]) {
+                            if (!flags[0] && dbg_in_bounds(rbg >= 0 && rbg < cp.nrb, p.status)) {
                                 const int old = atomicAdd(&cp.counters[rbg], 1);
                                 lastp = (old == (int)(gB - gA));
                                 if (lastp) cp.counters[rbg] = 0;
@@ -438,7 +451,7 @@ __device__ __forceinline__ void consume_class(const ClassParams &cp, unsigned ch
                             flags[1] = lastp;
                         }
                         named_bar_sync(1, K::NT);
-                        if (flags[1]) {
+                        if (flags[1] && dbg_in_bounds(gA >= 0 && gB + rbg < G + cp.nrb, p.status)) {
                             __threadfence();
                             constexpr int E = (K::KC * K::BM) / K::NT;
                             T sum[E];

@@ -128,7 +128,7 @@ __device__ __forceinline__ int bgroup(int j, int g) {
 // stores.
 template <class K>
 __device__ __forceinline__ void load_b_stage(const float *__restrict__ B, int64_t ldb, int64_t n, int k, int64_t j0,
-                                             float *brow, int lane) {
+                                             float *brow, int lane, unsigned *status) {
     constexpr int NG = K::KC / 4;
     constexpr int NBLK = (K::BNS / 4) * NG;
 #pragma unroll 1
@@ -140,7 +140,7 @@ __device__ __forceinline__ void load_b_stage(const float *__restrict__ B, int64_
         for (int i = 0; i < 4; ++i) {
             const int c = 4 * cg + i;
             const float *col = B + jr + (int64_t)c * ldb;
-            if (c >= k) {
+            if (c >= k || !dbg_in_bounds(jr >= 0 && c < K::KC, status)) {
                 v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             } else if (jr + 3 < n) {
                 v[i] = __ldg(reinterpret_cast<const float4 *>(col));

@@ -171,7 +171,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                 const int64_t u = u_begin + i;
                 const int64_t jc = u - (u / p.upr) * p.upr;
                 load_b_stage<K>(static_cast<const float *>(p.B), p.ldb, p.n, p.k, jc * K::BNS,
-                                reinterpret_cast<float *>(sBrow + (size_t)s * K::BROW_STAGE), lane);
+                                reinterpret_cast<float *>(sBrow + (size_t)s * K::BROW_STAGE), lane, p.status);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&full[s]);
             }
@@ -301,7 +301,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                                 const int slot = e / K::BM;
                                 const int row = e - slot * K::BM;
                                 const int c = (slot / K::CC) * K::KCW + r0 + (slot % K::CC);
-                                if (c < p.k)
+                                if (c < p.k && dbg_in_bounds(row0 + row + 3 < p.m, p.status))
                                     *reinterpret_cast<float4 *>(C + row0 + row + (int64_t)c * ldc) =
                                         *reinterpret_cast<const float4 *>(sRed + e);
                             }
@@ -338,7 +338,8 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                                     T tmp[K::V];
 #pragma unroll
                                     for (int e = 0; e < K::V; ++e) tmp[e] = acc[v * K::V + e][c];
-                                    *reinterpret_cast<vec_t *>(cw + row_of(v)) = K::VT::make(tmp);
+                                    if (dbg_in_bounds(row0 + row_of(v) + K::V - 1 < p.m && kbase + c < p.k, p.status))
+                                        *reinterpret_cast<vec_t *>(cw + row_of(v)) = K::VT::make(tmp);
                                 }
                                 cw += ldc;
                             }
@@ -352,7 +353,8 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                                         T tmp[K::V];
 #pragma unroll
                                         for (int e = 0; e < K::V; ++e) tmp[e] = acc[v * K::V + e][c];
-                                        *reinterpret_cast<vec_t *>(cw + row_of(v)) = K::VT::make(tmp);
+                                        if (dbg_in_bounds(row0 + row_of(v) + K::V - 1 < p.m, p.status))
+                                            *reinterpret_cast<vec_t *>(cw + row_of(v)) = K::VT::make(tmp);
                                     }
                                 }
                                 cw += ldc;
@@ -381,7 +383,8 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                             T tmp[K::V];
 #pragma unroll
                             for (int e = 0; e < K::V; ++e) tmp[e] = acc[v * K::V + e][c];
-                            __stcg(reinterpret_cast<vec_t *>(slot + c * K::BM + row_of(v)), K::VT::make(tmp));
+                            if (dbg_in_bounds(my_slot < G + (p.m + K::BM - 1) / K::BM, p.status))
+                                __stcg(reinterpret_cast<vec_t *>(slot + c * K::BM + row_of(v)), K::VT::make(tmp));
                         }
                 }
             } else {
@@ -413,7 +416,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                         const int c = c0 + cc;
                         if (whole) {
                             if (!aborted && c < p.k && row0 + row < p.m) C[row0 + row + (int64_t)c * p.ldc] = sum;
-                        } else {
+                        } else if (dbg_in_bounds(my_slot < G + (p.m + K::BM - 1) / K::BM, p.status)) {
                             __stcg(slot + c * K::BM + row, sum);
                         }
                     }
@@ -427,7 +430,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                 named_bar_sync(1, K::NT);
                 if (tid == 0) {
                     int last = 0;
-                    if (!flags[0]) {
+                    if (!flags[0] && dbg_in_bounds(rb64 < (p.m + K::BM - 1) / K::BM, p.status)) {
                         const int npieces = (int)(gB - gA + 1);
                         const int old = atomicAdd(&p.counters[rb], 1);
                         last = (old == npieces - 1);
@@ -436,7 +439,7 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                     flags[1] = last;
                 }
                 named_bar_sync(1, K::NT);
-                if (flags[1]) {
+                if (flags[1] && dbg_in_bounds(gA >= 0 && gB + rb64 < G + (p.m + K::BM - 1) / K::BM, p.status)) {
                     __threadfence();
                     if constexpr (K::WC == 1) {
 #pragma unroll

@@ -120,3 +120,16 @@ def test_tsm2x_schedule_choice(lib, elem, m, n, k, want):
 def test_tsm2x_choice_rejects_bad_arguments(lib):
     assert pkg.tsm2x_choice(2, 10, 10, 10) == ""
     assert pkg.tsm2x_choice(4, -1, 10, 10) == ""
+
+
+def test_debug_build_flag_exported(lib):
+    """The release library reports no bounds checks; the debug variant (when
+    built) reports them.  No device is needed for either call."""
+    assert lib.tsm2_debug_checks() == 0
+    import ctypes
+    import os
+    from paper_2002_03258_gb300 import build as b
+    if os.path.exists(b.DEBUG_LIB):
+        dbg = ctypes.CDLL(b.DEBUG_LIB)
+        dbg.tsm2_debug_checks.restype = ctypes.c_int
+        assert dbg.tsm2_debug_checks() == 1

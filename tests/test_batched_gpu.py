@@ -211,3 +211,35 @@ def test_batch_fullsize_workload_sampled(variant, merge, mode, pitch):
     plan.close()
     del bufs
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("mode", ["single", "serial"])
+def test_class_with_fewer_groups_than_blocks(mode):
+    """A TSM2R class whose work groups are fewer than the grid's blocks (one
+    777^2 problem with 12 columns: 100 stages) beside larger classes: in one
+    launch the class is shared by only as many blocks as it has groups, so
+    every partial sum its fix-up adds was written."""
+    import paper_2002_03258_gb300 as pkg
+    import paper_2002_03258_gb300.batched as bt
+    shapes = [("r", 3000, 3000, 16), ("r", 777, 777, 11), ("r", 300, 300, 3), ("l", 200001, 24, 24)]
+    items = []
+    for idx, (op, m, n, k) in enumerate(shapes):
+        A = ti.uniform_pm1(idx, ti.MID_A, m, n, np.float32)
+        B = ti.uniform_pm1(idx, ti.MID_B, n, k, np.float32)
+        lda, ldb = (m + 3) // 4 * 4, (n + 3) // 4 * 4
+        tA = torch.zeros((n, lda), device="cuda")
+        tB = torch.zeros((k, ldb), device="cuda")
+        tC = torch.full((k, lda), float("nan"), device="cuda")
+        tA.t()[:m].copy_(torch.from_numpy(np.ascontiguousarray(A)))
+        tB.t()[:n].copy_(torch.from_numpy(np.ascontiguousarray(B)))
+        items.append(dict(op=op, m=m, n=n, k=k, A=A, B=B, tA=tA, tB=tB, tC=tC,
+                          p=bt.problem(op, m, n, k, tA.data_ptr(), lda, tB.data_ptr(), ldb, tC.data_ptr(), lda)))
+    for v in range(bt.num_variants()):
+        plan = bt.BatchPlan([it["p"] for it in items], bt.variant_flag(v))
+        plan.set_mode(mode)
+        for it in items:
+            it["tC"].fill_(float("nan"))
+        plan.graph_launch(0)
+        assert pkg.tsm2_get_device_status(0) == 0
+        check_all(items)
+        plan.close()
