@@ -6,8 +6,10 @@ TSM2R with A n x n, n in {10240, 20480, 30720}, times B n x k, k in
 {2, 4, 8, 16}; and TSM2L with A m x n, m in {2^20, 2^23}, n in {8, 16, 32},
 times B n x n.  Entries are uniform in [-1, 1) from the splitmix64 generator,
 generated in device memory.  Every launch is preceded by an L2 flush (a
-memset of twice the L2 size) and timed on its stream with CUDA events; the
-step time is the sum of the 18 kernel durations.
+memset of twice the L2 size, then a read of another buffer of that size, so
+no operand and no dirty line is left in L2) and timed on its stream with CUDA
+events; the step time is the sum of the 18 kernel durations.  The same sweep
+behind the memset alone is reported beside it (``flush_write_only``).
 
 Metric: achieved HBM bandwidth, algorithmic bytes s*(m n + n k + m k) per
 multiply divided by kernel time, in GB/s (whole job: summed over ranks).
@@ -46,6 +48,27 @@ BATCH_PITCH_BYTES = 512     # batched workload: leading dimensions rounded up to
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 nominal FP64 (no FP64 tensor-core speed-up)
 NOMINAL_HBM_GBS = 8000.0     # GB300 HBM3e, nominal (~8 TB/s)
 FALLBACK_HBM_GBS = 6800.0
+
+
+def make_l2_flush(torch, device):
+    """(flush, write_only_flush) for the timed loops.  `flush` writes a buffer
+    of twice the L2 size (evicting every operand line) and then reads another
+    one, so the lines left in L2 are clean: after a write alone the timed
+    kernel would also pay for writing the flush's dirty lines back to DRAM
+    (measured: up to ~30 us on a 0.53 ms kernel).  `write_only_flush` is the
+    memset alone, reported beside the headline for comparison."""
+    l2 = getattr(torch.cuda.get_device_properties(device), "L2_cache_size", 128 << 20) or (128 << 20)
+    wbuf = torch.empty(2 * l2, dtype=torch.uint8, device=device)
+    rbuf = torch.ones(2 * l2 // 4, dtype=torch.float32, device=device)
+    sink = torch.zeros((), dtype=torch.float32, device=device)
+
+    def flush():
+        wbuf.zero_()
+        torch.sum(rbuf, dim=(0,), out=sink)
+
+    def write_only_flush():
+        wbuf.zero_()
+    return flush, write_only_flush
 
 
 def cases(dtype_bytes):
@@ -314,11 +337,7 @@ def run_gpu(args):
     sh = stream.cuda_stream
 
     props = torch.cuda.get_device_properties(dev)
-    l2 = getattr(props, "L2_cache_size", 128 << 20) or (128 << 20)
-    flush = torch.empty(2 * l2, dtype=torch.uint8, device=dev)
-
-    def l2_flush():
-        flush.zero_()
+    l2_flush, l2_flush_write_only = make_l2_flush(torch, dev)
 
     def make_sweep(es, seed):
         tdt = torch.float32 if es == 4 else torch.float64
@@ -350,10 +369,11 @@ def run_gpu(args):
         return w["fn"](w["m"], w["n"], w["k"], w["A"].data_ptr(), w["m"], w["B"].data_ptr(), w["n"],
                        w["C"].data_ptr(), w["m"], s)
 
-    def timed_steps(work, steps, warmup):
+    def timed_steps(work, steps, warmup, flush_fn=None):
+        flush_fn = flush_fn or l2_flush
         for _ in range(warmup):
             for w in work:
-                l2_flush()
+                flush_fn()
                 pkg.check(call(w))
         torch.cuda.synchronize()
         pkg.check(pkg.tsm2_get_device_status(sh))
@@ -366,7 +386,7 @@ def run_gpu(args):
         t_region0 = time.perf_counter()
         for s in range(steps):
             for i, w in enumerate(work):
-                l2_flush()
+                flush_fn()
                 evs[s][i][0].record(stream)
                 pkg.check(call(w))
                 evs[s][i][1].record(stream)
@@ -413,6 +433,17 @@ def run_gpu(args):
                 "frac": round(achieved / peak_hbm, 4), "traffic": traffic,
                 "kernel": case_cfg.get(dom), "workload": wkey, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": dw["bytes"]}
+
+    # ---- the same sweep behind the write-only flush (comparison) -----------------------
+    wo_steps = max(1, min(args.steps, 3))
+    per_wo, _, _ = timed_steps(work32, wo_steps, 1, l2_flush_write_only)
+    wo_ms = ranks_max(statistics.mean(sum(row) for row in per_wo), dev, world)
+    wo_dom = statistics.mean(per_wo[s_][dom] for s_ in range(wo_steps))
+    flush_write_only = {"value": round(job_gbs(world, step_bytes, wo_ms), 2), "unit": "GB/s",
+                        "ms_per_step": round(wo_ms, 4), "steps": wo_steps,
+                        "dominant_kernel_ms": round(wo_dom, 4),
+                        "dominant_kernel_frac": round(dw["bytes"] / (wo_dom * 1e-3) / 1e9 / peak_hbm, 4),
+                        "l2": "memset of 2x L2 before every launch, no read pass"}
 
     # ---- end to end through the C ABI with host buffers --------------------------------------
     # tsm2r_s_host / tsm2l_s_host: A, B, C in page-locked host memory; each
@@ -788,12 +819,14 @@ def run_gpu(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(mean_step_ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (device-generated splitmix64 uniform[-1,1))",
-        "config": {"workload": WORKLOAD, "l2": "flushed before every launch (memset of 2x L2)",
+        "config": {"workload": WORKLOAD,
+                   "l2": "flushed before every launch: memset of 2x L2, then a read of another 2x L2 buffer "
+                         "(no operand and no dirty line of the flush left in L2)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "step_wall_s": round(wall / args.steps, 4)},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
         "clocks": clock_rec, "fp64": fp64, "fwd_bwd": fwd_bwd, "mixed_precision": mixed, "batched": batched,
-        "crossover": crossover, "cases": case_rows,
+        "crossover": crossover, "cases": case_rows, "flush_write_only": flush_write_only,
         "src_hash": src_hash(),
     }
     if rank == 0:
@@ -843,11 +876,10 @@ def run_case(args):
         fn = getattr(pkg, f"tsm2{op}_{suf}")
         A_ptr = A.data_ptr()
         nbytes = alg_bytes(m, n, k, es)
-    l2 = getattr(torch.cuda.get_device_properties(0), "L2_cache_size", 128 << 20) or (128 << 20)
-    flush = torch.empty(2 * l2, dtype=torch.uint8, device="cuda")
+    l2_flush, _ = make_l2_flush(torch, 0)
     ts = []
     for r in range(args.warmup + args.steps):
-        flush.zero_()
+        l2_flush()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         pkg.check(fn(m, n, k, A_ptr, m, B.data_ptr(), n, C.data_ptr(), m, 0))
@@ -945,11 +977,10 @@ def run_batch_case(args):
         probs.append(bt.problem(o, m, n, k, tA.data_ptr(), lda, tB.data_ptr(), ldb, tC.data_ptr(), lda))
         total += 4 * (m * n + n * k + m * k)
     plan = bt.BatchPlan(probs, flags)
-    l2 = getattr(torch.cuda.get_device_properties(0), "L2_cache_size", 128 << 20) or (128 << 20)
-    flush = torch.empty(2 * l2, dtype=torch.uint8, device="cuda")
+    l2_flush, _ = make_l2_flush(torch, 0)
     ts = []
     for r in range(args.warmup + args.steps):
-        flush.zero_()
+        l2_flush()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         plan.execute(0)

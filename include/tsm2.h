@@ -60,7 +60,12 @@
  *    happen while the stream is captured into a CUDA graph: a call that
  *    would grow the workspace during capture returns TSM2_ERR_UNSUPPORTED
  *    (the capture itself stays valid).  Call the largest shape once on the
- *    stream before capturing.
+ *    stream before capturing.  TSM2L with B on chip (n <= 64) hands out
+ *    its row blocks at run time through two counters of the same workspace
+ *    (allocated on the first such call on a stream); while a stream without
+ *    a workspace is captured it uses the static partition instead.  Either
+ *    way every row block is computed whole by one thread block in the same
+ *    order, so the result is the same bits.
  */
 #ifndef TSM2_H
 #define TSM2_H
@@ -392,6 +397,16 @@ void tsm2_set_path(int path);
  * SM, limited so each block gets at least a few work units). */
 void tsm2_set_grid(int blocks);
 
+/* Work partition of TSM2L with B on chip: 0 = row blocks claimed at run
+ * time from an atomic counter, each block starting with its own (default:
+ * blocks on SMs that stream faster take more row blocks); 1 = a static
+ * partition, equal contiguous runs of row blocks.  Every row block is
+ * computed whole by one thread block in the same order either way, so the
+ * results are bitwise equal.  (The configuration that stages C through
+ * shared memory, lw_f32_kc16, always uses the static partition.)  TSM2R
+ * always uses its static partition. */
+void tsm2_set_balance(int mode);
+
 /* How the host-operand entry points move page-locked buffers: 0 = copy
  * kernels on the SMs where the device can address the buffer (default),
  * 1 = always the copy engines.  Other values select 0. */
@@ -401,7 +416,9 @@ void tsm2_set_host_copy(int mode);
  * every later launch whose grid has at most `blocks` blocks writes four
  * 64-bit words per block b into device memory at device_words[4b..4b+3]:
  * start time, time the first stage arrived, end time (ns, %globaltimer),
- * and the number of work units the block processed.  NULL turns it off.
+ * and the number of work units the block processed (low 32 bits; with
+ * TSM2L row blocks claimed at run time also the index of the SM the block
+ * ran on in the high 32 bits, else 0 there).  NULL turns it off.
  * The buffer is caller-owned device memory. */
 void tsm2_set_trace(unsigned long long *device_words, int64_t blocks);
 

@@ -108,6 +108,8 @@ def _load():
             lib.tsm2_set_grid.argtypes = [ctypes.c_int]
             lib.tsm2_set_host_copy.argtypes = [ctypes.c_int]
             lib.tsm2_set_host_copy.restype = None
+            lib.tsm2_set_balance.argtypes = [ctypes.c_int]
+            lib.tsm2_set_balance.restype = None
             lib.tsm2_set_trace.argtypes = [vp, i64]
             lib.tsm2_set_trace.restype = None
             for name in ("tsm2_fill_uniform_d", "tsm2_fill_uniform_s", "tsm2_fill_int_small_d",
@@ -244,6 +246,10 @@ def tsm2_set_host_copy(mode: int) -> None:
     _load().tsm2_set_host_copy(int(mode))
 
 
+def tsm2_set_balance(mode: int) -> None:
+    _load().tsm2_set_balance(int(mode))
+
+
 def tsm2_set_trace(device_words, blocks: int) -> None:
     _load().tsm2_set_trace(device_words, int(blocks))
 
@@ -347,7 +353,7 @@ __all__ = [
     "tsm2r_d", "tsm2r_s", "tsm2l_d", "tsm2l_s", "tsm2r_s_noalloc", "tsm2_get_last_error_string", "tsm2_last_config",
     "tsm2r_s_host", "tsm2r_d_host", "tsm2l_s_host", "tsm2l_d_host", "tsm2x_s", "tsm2x_d", "tsm2x_choice",
     "tsm2_get_device_status", "tsm2_shutdown", "tsm2_set_wait_budget_ns", "tsm2_set_path", "tsm2_set_grid", "tsm2_set_trace",
-    "tsm2_set_host_copy", "tsm2_last_host_copy",
+    "tsm2_set_host_copy", "tsm2_last_host_copy", "tsm2_set_balance",
     "check", "tsm2r", "tsm2l", "tsm2r_t", "rankk", "empty_colmajor", "TSM2Error", "lib", "LIB_PATH",
     "tsm2r_t_d", "tsm2r_t_s", "tsm2_rankk_d", "tsm2_rankk_s", "tsm2r_bf16", "tsm2_split_bf16",
 ]

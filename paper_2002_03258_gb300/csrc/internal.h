@@ -28,6 +28,7 @@ struct StreamLaunch {
     CUtensorMap mapB;   // B: dims {n, k}, box {BNS, KC} (unused when B is resident)
     void *ws;           // partial-sum slots, 256-byte aligned
     int *counters;      // one arrival counter per row block, zero between launches
+    int *claims;        // resident-B schedules: row-block claim counters, zero between launches (nullptr: static)
     unsigned *status;   // device status word
     int64_t wait_ns;    // bound of every pipeline wait
     int grid;           // thread blocks of the persistent grid

@@ -31,6 +31,7 @@ int64_t g_wait_ns = 1000000000LL;
 int g_path = 0;
 int g_grid_override = 0;
 int g_host_copy = 0;               // 0: SM copies for device-mapped page-locked host buffers; 1: copy engines
+int g_balance = 0;                 // 0: TSM2L row blocks claimed at run time; 1: static partition
 thread_local int t_grid_cap = 0;   // > 0: upper bound of the product kernels' persistent grid (this thread)
 unsigned long long *g_trace = nullptr;
 int64_t g_trace_blocks = 0;
@@ -128,6 +129,32 @@ tsm2_status workspace(cudaStream_t stream, size_t counter_bytes, size_t slot_byt
     *counters = static_cast<int *>(w.ptr);
     *ws = static_cast<char *>(w.ptr) + w.counter_bytes;
     return TSM2_SUCCESS;
+}
+
+// Claim counters of the resident-B schedules: the first two counters of the
+// stream's workspace (zero between launches; the kernel rearms them).  While
+// the stream is being captured a workspace cannot be created, and the launch
+// then keeps the static partition (nullptr).
+tsm2_status claim_counters(cudaStream_t stream, int **claims) {
+    *claims = nullptr;
+    if (g_balance == 1) return TSM2_SUCCESS;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_ws.find({dev, reinterpret_cast<uintptr_t>(stream)});
+        if (it != g_ws.end() && it->second.ptr && it->second.counter_bytes >= 2 * sizeof(int)) {
+            *claims = static_cast<int *>(it->second.ptr);
+            return TSM2_SUCCESS;
+        }
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone) return TSM2_SUCCESS;
+    void *ws = nullptr;
+    return workspace(stream, 2 * sizeof(int), 0, &ws, claims);
 }
 
 // ---- tensor maps -----------------------------------------------------------
@@ -325,6 +352,10 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
         }
         L.ws = ws;
         L.counters = counters;
+        if (shape->b_resident) {
+            st = claim_counters(stream, &L.claims);
+            if (st != TSM2_SUCCESS) return st;
+        }
         L.status = dev->status;
         L.wait_ns = g_wait_ns;
         L.c_vec = aligned16(g.C) && ((ldc * elem) % 16 == 0);
@@ -1538,6 +1569,8 @@ void tsm2_set_path(int path) { g_path = path; }
 void tsm2_set_grid(int blocks) { g_grid_override = blocks < 0 ? 0 : blocks; }
 
 void tsm2_set_host_copy(int mode) { g_host_copy = mode == 1 ? 1 : 0; }
+
+void tsm2_set_balance(int mode) { g_balance = mode == 1 ? 1 : 0; }
 
 void tsm2_set_trace(unsigned long long *device_words, int64_t blocks) {
     g_trace = device_words;

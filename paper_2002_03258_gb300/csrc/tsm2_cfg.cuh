@@ -90,7 +90,11 @@ struct Cfg {
     // bytes) and, with loaded B, one loader warp's.
     static constexpr int FULL_ARRIVALS = BLOAD ? 2 : 1;
     static constexpr size_t OFF_FLAGS = OFF_BAR + NBAR * STAGES * sizeof(uint64_t);
-    static constexpr size_t SMEM = OFF_FLAGS + 32 + 128;  // + slack for 128-byte alignment
+    // Resident B without the staged epilogue: row blocks can be claimed at
+    // run time, and meta[] holds the row block of every stage.
+    static constexpr bool DYN = BRES_ && !SEPI_;
+    static constexpr size_t OFF_META = OFF_FLAGS + 32;
+    static constexpr size_t SMEM = OFF_META + (DYN ? align_up(STAGES * sizeof(int), 16) : 0) + 128;  // + slack for 128-byte alignment
 
     static_assert(BT || JW % JV == 0, "a warp's columns must be whole B vectors");
     static_assert((BNS * sizeof(T)) % 16 == 0, "TMA inner box extent must be 16-byte multiple");
@@ -129,7 +133,7 @@ __device__ __forceinline__ int bgroup(int j, int g) {
 template <class K>
 __device__ __forceinline__ void load_b_stage(const float *__restrict__ B, int64_t ldb, int64_t n, int k, int64_t j0,
                                              float *brow, int lane, unsigned *status) {
-    constexpr int NG = K::KC / 4;
+    constexpr int NG = K::KC >= 4 ? K::KC / 4 : 1;  // (instantiated, never run, for KC < 4)
     constexpr int NBLK = (K::BNS / 4) * NG;
 #pragma unroll 1
     for (int u = lane; u < NBLK; u += 32) {

@@ -44,6 +44,7 @@
 #include "internal.h"
 #include "tsm2_cfg.cuh"
 
+#include <climits>
 #include <mutex>
 
 namespace tsm2 {
@@ -58,6 +59,11 @@ struct Params {
     void *C;
     int64_t ldc;
     void *ws;
+    // Split row blocks: one arrival counter per row block.  Resident-B
+    // (TSM2L) schedules, which split nothing, use counters[0..1] to hand out
+    // row blocks at run time instead: [0] counts the row blocks claimed
+    // beyond the first one of every block, [1] the blocks that have claimed
+    // their last.  Zero between launches; nullptr: the static partition.
     int *counters;
     unsigned *status;
     int64_t wait_ns;
@@ -65,7 +71,7 @@ struct Params {
     int64_t gran;     // units per indivisible group
     int64_t ngroups;  // groups in total
     int c_vec;
-    unsigned long long *trace;  // optional: 4 words per block (start, first data, end, units)
+    unsigned long long *trace;  // optional: 4 words per block (start, first data, end, units [| SM << 32])
 };
 
 template <class K>
@@ -87,6 +93,13 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     // hoist per-column address offsets out of the unit loop (they would sit in
     // registers next to the accumulators).
     volatile int64_t *s_ldc = reinterpret_cast<volatile int64_t *>(smem + K::OFF_FLAGS + 16);
+    // Row block of every stage when row blocks are claimed at run time.
+    volatile int *meta = reinterpret_cast<volatile int *>(smem + K::OFF_META);
+    // Not with the staged epilogue (lw_f32_kc16): its consumer warps would
+    // have to agree on every claimed row block at a barrier (a timed-out
+    // warp cannot follow the claims), which measured slower than the
+    // static partition.
+    const bool dyn = K::DYN && p.counters != nullptr;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -123,8 +136,58 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             int s = 0;
             uint32_t ph = 0;
             uint32_t issued = 0, last_par = 0;  // per-stage: issued at least once, parity of last issue
-            const int nunits = (int)(u_end - u_begin);
             const int upr = (int)p.upr;
+            if constexpr (K::DYN) {
+              if (dyn) {
+                // Whole row blocks claimed at run time: block g starts with row
+                // block g, then takes G + (the claim counter's old value) until
+                // the row blocks run out.  Each claim is issued a row block
+                // ahead of its use, so its round trip overlaps the copies.
+                // Every stage carries its row block in meta[]; a final stage
+                // with row block -1 and no bytes tells the consumers to stop.
+                // The result does not depend on who computes a row block.
+                // (Few live registers: this lane runs with the producer's 40.)
+                int rb = (int)g;
+                while (rb < (int)p.ngroups) {
+                    const int claim = atomicAdd(&p.counters[0], 1);
+                    for (int jc = 0; jc < upr; ++jc) {
+                        if (flags[0] || !mbar_wait_bounded(&empty[s], ph ^ 1u, p.wait_ns, flags)) {
+                            flags[0] = 1;
+                            atomicOr(p.status, kStatusTimeout);
+                            break;
+                        }
+                        meta[s] = rb;
+                        mbar_arrive_expect_tx(&full[s], K::TX_BYTES);
+                        T *dstA = sA + (size_t)s * K::A_STAGE;
+#pragma unroll
+                        for (int q = 0; q < K::NBOX; ++q)
+                            tma_load_2d_hint(dstA + q * K::BOXM * K::BNS, &mapA, rb * K::BM + q * K::BOXM,
+                                             jc * K::BNS, &full[s], policy);
+                        issued |= 1u << s;
+                        last_par = (last_par & ~(1u << s)) | (ph << s);
+                        if (++s == K::STAGES) { s = 0; ph ^= 1u; }
+                    }
+                    rb = flags[0] ? INT_MAX : (int)G + claim;
+                }
+                if (!flags[0] && mbar_wait_bounded(&empty[s], ph ^ 1u, p.wait_ns, flags)) {
+                    meta[s] = -1;
+                    mbar_arrive(&full[s]);
+                    issued |= 1u << s;
+                    last_par = (last_par & ~(1u << s)) | (ph << s);
+                } else {
+                    flags[0] = 1;
+                    atomicOr(p.status, kStatusTimeout);
+                }
+                // This block's claims are done; the last block to get here
+                // rearms both counters for the next launch.
+                __threadfence();
+                if (atomicAdd(&p.counters[1], 1) == (int)G - 1) {
+                    p.counters[0] = 0;
+                    p.counters[1] = 0;
+                }
+              }
+            }
+            const int nunits = dyn ? 0 : (int)(u_end - u_begin);
             int rb = (int)(u_begin / p.upr);
             int jc = (int)(u_begin - (int64_t)rb * p.upr);
             for (int i = 0; i < nunits; ++i) {
@@ -207,10 +270,12 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     bool aborted = false;
     // Unit bookkeeping in 32 bits (a block's run is far below 2^31 units;
     // the host checks): registers are the scarce resource here.
-    const int nunits = (int)(u_end - u_begin);
+    // With row blocks claimed at run time the count is open-ended: the
+    // producer's end marker stops the loop.
+    const int nunits = (K::DYN && dyn) ? INT_MAX : (int)(u_end - u_begin);
     const int upr = (int)p.upr;
-    int rb = (int)(u_begin / p.upr);
-    int jc = (int)(u_begin - (int64_t)rb * p.upr);
+    int rb = (K::DYN && dyn) ? 0 : (int)(u_begin / p.upr);
+    int jc = (K::DYN && dyn) ? 0 : (int)(u_begin - (int64_t)rb * p.upr);
     bool piece_at_rb_start = (jc == 0);
 
     for (int i = 0; i < nunits; ++i) {
@@ -227,6 +292,21 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                     atomicOr(p.status, kStatusTimeout);
                 }
             }
+        }
+        if constexpr (K::DYN) {
+          if (dyn) {
+            // (No named barriers in the loop of these configurations: a warp
+            // that gave up can leave at once.)
+            if (aborted) break;
+            if (jc == 0) {
+                rb = meta[s];
+                if (rb < 0) {
+                    if (p.trace && threadIdx.x == 128)
+                        p.trace[4 * g + 3] = (unsigned long long)i | ((unsigned long long)sm_id() << 32);
+                    break;
+                }
+            }
+          }
         }
         if (!aborted) {
             const T *a_st = sA + (size_t)s * K::A_STAGE;
@@ -524,7 +604,7 @@ cudaError_t launch_cfg(const StreamLaunch &L, cudaStream_t stream) {
     p.C = L.g.C;
     p.ldc = L.g.ldc;
     p.ws = L.ws;
-    p.counters = L.counters;
+    p.counters = K::DYN ? L.claims : L.counters;
     p.status = L.status;
     p.wait_ns = L.wait_ns;
     const int64_t num_rb = (L.g.m + K::BM - 1) / K::BM;
