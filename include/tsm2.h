@@ -397,14 +397,13 @@ void tsm2_set_path(int path);
  * SM, limited so each block gets at least a few work units). */
 void tsm2_set_grid(int blocks);
 
-/* Work partition of TSM2L with B on chip: 0 = row blocks claimed at run
- * time from an atomic counter, each block starting with its own (default:
- * blocks on SMs that stream faster take more row blocks); 1 = a static
- * partition, equal contiguous runs of row blocks.  Every row block is
+/* Work partition of TSM2L with B on chip (n <= 64): 0 = row blocks claimed
+ * at run time from an atomic counter, each block starting with its own
+ * (default: blocks on SMs that stream faster take more row blocks); 1 = a
+ * static partition, equal contiguous runs of row blocks.  Every row block is
  * computed whole by one thread block in the same order either way, so the
- * results are bitwise equal.  (The configuration that stages C through
- * shared memory, lw_f32_kc16, always uses the static partition.)  TSM2R
- * always uses its static partition. */
+ * results are bitwise equal.  TSM2R and TSM2L with staged B (n > 64) always
+ * use their static partitions. */
 void tsm2_set_balance(int mode);
 
 /* How the host-operand entry points move page-locked buffers: 0 = copy

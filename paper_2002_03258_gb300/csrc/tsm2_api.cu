@@ -308,11 +308,10 @@ tsm2_status gemm(const char *fn, char op, int elem, int64_t m, int64_t n, int64_
         if (staged_l && kc < 4) kc = 4;  // staged-B TSM2L: C columns in groups of four
         const StreamShape *shape = stream_shape(elem, staged_l ? 't' : op, kc);
         if (op == 'l' && !staged_l) {
-            // Tall A: the 8-rows-per-lane schedule once every SM gets enough
-            // of its (larger) row blocks.  Measured on GB300: 12 C columns
-            // per lane (KC = 24) win from about 1.5 row blocks per SM (5-11%
-            // at 2^18 .. 2^20 rows, a tie below); the other widths need
-            // about 6 for an even spread.
+            // Tall A and wide C: the 8-rows-per-lane schedule (KC = 24, 32)
+            // once every SM gets enough of its (larger) row blocks.  Measured
+            // on GB300: KC = 24 wins from about 1.5 row blocks per SM (5-11%
+            // at 2^18 .. 2^20 rows, a tie below), KC = 32 needs about 6.
             const StreamShape *wide = stream_shape(elem, 'w', kc);
             const int64_t min_rb_per_sm = kc == 24 ? 1 : 6;
             if (wide && (m + wide->BM - 1) / wide->BM >= min_rb_per_sm * (int64_t)dev->sm_count) shape = wide;

@@ -366,17 +366,16 @@ template <int KC>
 using L32 = Cfg<float, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, TSM2_L_STAGES, true, 64,
                 (TSM2_L_BT != 0 && (KC / (KC >= 32 ? 2 : 1)) % 4 == 0)>;
 template <int KC> using L64 = Cfg<double, KC, 1, (KC >= 32 ? 4 : 8), 1, (KC >= 32 ? 2 : 1), 8, 5, true, 64>;
-// TSM2L schedule for tall A (binary32): R = 8 rows per lane, so every B value
-// read from shared memory (one wavefront per broadcast value) feeds twice the
-// FMAs; the C columns are split over WK = 1 or 2 warps.  Chosen when there are
-// enough row blocks for an even spread over the SMs.
-// KC = 32: 16 C columns per lane (128 accumulators, WK = 2, 1024-row blocks),
+// TSM2L schedule for tall A and wide C (binary32, KC = 24 and 32): R = 8 rows
+// per lane, so every B value read from shared memory (one wavefront per
+// broadcast value) feeds twice the FMAs; the C columns are split over WK = 2
+// warps.  Chosen when there are enough row blocks for an even spread over the
+// SMs.  KC = 32: 16 C columns per lane (128 accumulators, 1024-row blocks),
 // stored straight from registers.  n = k = 32 is FMA-bound on chip (32 FMAs
 // per 8 bytes of A and C), and against 8 columns per lane this halves the
-// shared-memory reads of A per FMA: 75% -> 92% of HBM at 2^23 rows.
-// KC = 16 keeps 16 C columns per lane (128 accumulators, WK = 1) and writes C
-// through shared memory (SEPI), measured faster than storing from registers
-// for this shape.
+// shared-memory reads of A per FMA: 75% -> 92% of HBM at 2^23 rows.  (For KC
+// <= 16 the 4-rows-per-lane schedule with row blocks claimed at run time
+// measured equal or faster at every height, up to 9% at 2^23 x 16.)
 struct WShape {
     int nv, wr, wk, jw, st;
     bool sepi;
@@ -385,10 +384,8 @@ struct WShape {
 #define TSM2_W_STAGES 5
 #endif
 constexpr WShape w32_shape(int kc) {
-    return kc >= 32   ? WShape{2, 4, 2, 8, TSM2_W_STAGES, false}   // 16 columns per lane
-           : kc >= 24 ? WShape{2, 4, 2, 8, TSM2_W_STAGES, false}   // 12 columns per lane
-           : kc >= 16 ? WShape{2, 8, 1, 4, TSM2_W_STAGES, true}
-                      : WShape{2, 8, 1, 4, TSM2_W_STAGES, false};
+    return kc >= 32 ? WShape{2, 4, 2, 8, TSM2_W_STAGES, false}   // 16 columns per lane
+                    : WShape{2, 4, 2, 8, TSM2_W_STAGES, false};  // KC = 24: 12 columns per lane
 }
 template <int KC>
 using W32 = Cfg<float, KC, w32_shape(KC).nv, w32_shape(KC).wr, 1, w32_shape(KC).wk, w32_shape(KC).jw,

@@ -95,10 +95,9 @@ stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     volatile int64_t *s_ldc = reinterpret_cast<volatile int64_t *>(smem + K::OFF_FLAGS + 16);
     // Row block of every stage when row blocks are claimed at run time.
     volatile int *meta = reinterpret_cast<volatile int *>(smem + K::OFF_META);
-    // Not with the staged epilogue (lw_f32_kc16): its consumer warps would
-    // have to agree on every claimed row block at a barrier (a timed-out
-    // warp cannot follow the claims), which measured slower than the
-    // static partition.
+    // (Not with the staged epilogue, whose consumer warps would have to agree
+    // on every claimed row block at a barrier: a timed-out warp cannot follow
+    // the claims.  Only staged-B TSM2L stages C, and it keeps static runs.)
     const bool dyn = K::DYN && p.counters != nullptr;
 
     const int warp = threadIdx.x >> 5;
@@ -655,10 +654,7 @@ const Entry kEntries[] = {
     TSM2_ENTRY('l', L64<4>, "l_f64_kc4"),    TSM2_ENTRY('l', L64<8>, "l_f64_kc8"),
     TSM2_ENTRY('l', L64<12>, "l_f64_kc12"),  TSM2_ENTRY('l', L64<16>, "l_f64_kc16"),
     TSM2_ENTRY('l', L64<24>, "l_f64_kc24"),  TSM2_ENTRY('l', L64<32>, "l_f64_kc32"),
-    TSM2_ENTRY('w', W32<2>, "lw_f32_kc2"),   TSM2_ENTRY('w', W32<4>, "lw_f32_kc4"),
-    TSM2_ENTRY('w', W32<8>, "lw_f32_kc8"),   TSM2_ENTRY('w', W32<12>, "lw_f32_kc12"),
-    TSM2_ENTRY('w', W32<16>, "lw_f32_kc16"), TSM2_ENTRY('w', W32<24>, "lw_f32_kc24"),
-    TSM2_ENTRY('w', W32<32>, "lw_f32_kc32"),
+    TSM2_ENTRY('w', W32<24>, "lw_f32_kc24"), TSM2_ENTRY('w', W32<32>, "lw_f32_kc32"),
     TSM2_ENTRY('t', T32<4>, "lt_f32_kc4"),   TSM2_ENTRY('t', T32<8>, "lt_f32_kc8"),
     TSM2_ENTRY('t', T32<12>, "lt_f32_kc12"), TSM2_ENTRY('t', T32<16>, "lt_f32_kc16"),
     TSM2_ENTRY('t', T32<24>, "lt_f32_kc24"), TSM2_ENTRY('t', T32<32>, "lt_f32_kc32"),

@@ -19,14 +19,13 @@ pytestmark = pytest.mark.gpu
 
 from gpu_util import DevMat, assert_parity, call  # noqa: E402
 
-# (dtype, m, n, k, configuration prefix): resident-B shapes of every kind
-# (lw_f32_kc16, which stages C through shared memory, keeps the static
-# partition in both modes).
+# (dtype, m, n, k, configuration prefix): resident-B shapes of every kind.
 SHAPES = [
     (np.float32, 300001, 8, 8, "l_f32_kc8"),
-    (np.float32, 2000003, 16, 16, "lw_f32_kc16"),
+    (np.float32, 2000003, 16, 16, "l_f32_kc16"),
     (np.float32, 1 << 20, 32, 32, "lw_f32_kc32"),
-    (np.float32, 2000003, 8, 8, "lw_f32_kc8"),
+    (np.float32, 2000003, 12, 10, "l_f32_kc12"),
+    (np.float32, 3000001, 3, 2, "l_f32_kc2"),
     (np.float32, 200000, 24, 20, "lw_f32_kc24"),
     (np.float32, 99999, 64, 5, "l_f32_kc8"),
     (np.float64, 500001, 16, 16, "l_f64_kc16"),

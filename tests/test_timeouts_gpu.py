@@ -47,7 +47,7 @@ def expect_timeout_then_recover(run, check):
     ("r", np.float64, 3000, 6000, 8, "r_f64"),
     ("r", np.float32, 4096, 8192, 12, "r_f32_kc12"),
     ("l", np.float32, 1 << 21, 32, 32, "l"),
-    ("l", np.float32, 1 << 21, 16, 16, "lw_f32_kc16"),
+    ("l", np.float32, 1 << 21, 16, 16, "l_f32_kc16"),
     ("l", np.float64, 1 << 21, 16, 16, "l"),
     ("l", np.float32, 1 << 19, 200, 16, "lt_f32"),
 ])
