@@ -434,6 +434,23 @@ def run_gpu(args):
                 "kernel": case_cfg.get(dom), "workload": wkey, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": dw["bytes"]}
 
+    # ---- the launch floor: the same flush and event pair around a trivial kernel ------
+    def floor_us(fn, reps=30):
+        ts = []
+        for _ in range(reps + 5):
+            l2_flush()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        return round(statistics.median(ts[5:]), 2)
+    one = torch.zeros(1, device=dev)
+    launch_floor = {"events_only_us": floor_us(lambda: None), "trivial_kernel_us": floor_us(lambda: one.add_(1.0)),
+                    "note": "CUDA-event time of an empty region and of a one-element kernel after the same L2 "
+                            "flush: the part of every timed call that is launch and completion"}
+
     # ---- the same sweep behind the write-only flush (comparison) -----------------------
     wo_steps = max(1, min(args.steps, 3))
     per_wo, _, _ = timed_steps(work32, wo_steps, 1, l2_flush_write_only)
@@ -827,6 +844,7 @@ def run_gpu(args):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
         "clocks": clock_rec, "fp64": fp64, "fwd_bwd": fwd_bwd, "mixed_precision": mixed, "batched": batched,
         "crossover": crossover, "cases": case_rows, "flush_write_only": flush_write_only,
+        "launch_floor": launch_floor,
         "src_hash": src_hash(),
     }
     if rank == 0:

@@ -411,9 +411,11 @@ void tsm2_set_balance(int mode);
  * 1 = always the copy engines.  Other values select 0. */
 void tsm2_set_host_copy(int mode);
 
-/* Per-block timeline of the bulk-copy kernels, for profiling.  When set,
- * every later launch whose grid has at most `blocks` blocks writes four
- * 64-bit words per block b into device memory at device_words[4b..4b+3]:
+/* Per-block timeline of the bulk-copy kernels and of the batched kernel,
+ * for profiling.  When set, every later launch whose grid has at most
+ * `blocks` blocks writes four 64-bit words per block b into device memory at
+ * device_words[4b..4b+3] (the batched kernel writes only the start and end
+ * times, the other two stay as they were):
  * start time, time the first stage arrived, end time (ns, %globaltimer),
  * and the number of work units the block processed (low 32 bits; with
  * TSM2L row blocks claimed at run time also the index of the SM the block

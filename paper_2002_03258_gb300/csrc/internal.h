@@ -154,6 +154,7 @@ struct BatchKParams {
     ClassParams cls[kMaxBatchMenu];  // slot i of the kernel's menu
     unsigned *status;
     int64_t wait_ns;
+    unsigned long long *trace;  // optional: 4 words per block (start, 0, end, 0); nullptr: off
 };
 
 struct BatchClass {

@@ -685,6 +685,7 @@ tsm2_status launch_classes(tsm2_batch_plan_s *P, int lo, int hi, int grid, cudaS
     for (int i = lo; i < hi; ++i) class_params(P->classes[i], kp.cls[P->classes[i].slot]);
     kp.status = dev->status;
     kp.wait_ns = g_wait_ns;
+    kp.trace = (g_trace && g_trace_blocks >= grid) ? g_trace : nullptr;
     const cudaError_t e = P->menu->launch(kp, grid < 1 ? 1 : grid, stream);
     return e == cudaSuccess ? TSM2_SUCCESS : cuda_error(e, "batch kernel launch");
 }

@@ -513,6 +513,7 @@ __global__ void __launch_bounds__(384, 1) batch_kernel(const __grid_constant__ B
     const int lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
+        if (p.trace) p.trace[4 * blockIdx.x] = globaltimer_ns();
         for (int s = 0; s < LY::STAGES; ++s) {
             mbar_init(&full[s], 2);  // the producer lane's copy and one loader warp
             mbar_init(&empty[s], 8);
@@ -552,6 +553,7 @@ __global__ void __launch_bounds__(384, 1) batch_kernel(const __grid_constant__ B
     bool aborted = false;
     int ci = 0;
     (consume_class<Ks, LY>(p.cls[ci++], smem, full, empty, flags, p, ring, aborted), ...);
+    if (p.trace && threadIdx.x == 128) p.trace[4 * blockIdx.x + 2] = globaltimer_ns();
 }
 
 template <int PREG, class... Ks>
