@@ -171,3 +171,51 @@ def test_capture_without_workspace_uses_static_partition():
         assert torch.equal(dC.view, ref)
     assert pkg.tsm2_get_device_status(0) == 0
 
+
+
+def test_several_column_passes():
+    """k = 80: three launches (32 + 32 + 16 columns of C), each claiming the
+    row blocks afresh from the rearmed counters."""
+    dtype, m, n, k = np.float32, 500001, 24, 80
+    A, B, dA, dB, dC, out = run_both(dtype, m, n, k, "l_f32_kc16")
+    assert torch.equal(out[0], out[1])
+    assert not torch.isnan(out[0]).any()
+    rows = sample_rows(m, 1500, seed=5)
+    got = out[0][torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert_parity(got, np.ascontiguousarray(A[rows]), B, dtype)
+
+
+def test_timeout_while_claiming_then_recover():
+    """Single-attempt waits on a tall shape: blocks give up part-way through
+    their claims; the status reports the timeout once, the host clears the
+    counters, and the next calls give the static partition's bits again."""
+    import paper_2002_03258_gb300 as pkg
+    pkg.tsm2_set_path(0)
+    pkg.tsm2_set_grid(0)
+    m, n, k = 1 << 22, 16, 16
+    A = ti.uniform_pm1(10, ti.MID_A, m, n, np.float32)
+    B = ti.uniform_pm1(10, ti.MID_B, n, k, np.float32)
+    dA, dB, dC = DevMat(A), DevMat(B), DevMat(np.zeros((m, k), np.float32))
+    pkg.tsm2_set_wait_budget_ns(0)
+    try:
+        assert call("l", np.float32, m, n, k, dA, dB, dC) == 0
+        st = pkg.tsm2_get_device_status(0)
+    finally:
+        pkg.tsm2_set_wait_budget_ns(1_000_000_000)
+    assert pkg.tsm2_last_config() == "l_f32_kc16"
+    assert st in (0, pkg.ERR_TIMEOUT)
+    assert pkg.tsm2_get_device_status(0) == 0
+    outs = {}
+    try:
+        for mode in (1, 0, 0):
+            pkg.tsm2_set_balance(mode)
+            dC.view.fill_(float("nan"))
+            assert call("l", np.float32, m, n, k, dA, dB, dC) == 0
+            assert pkg.tsm2_get_device_status(0) == 0
+            outs.setdefault(mode, []).append(dC.view.clone())
+    finally:
+        pkg.tsm2_set_balance(0)
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][0])
+    rows = sample_rows(m, 1500, seed=6)
+    got = outs[0][0][torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert_parity(got, np.ascontiguousarray(A[rows]), B, np.float32)
