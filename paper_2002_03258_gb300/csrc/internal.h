@@ -144,10 +144,31 @@ constexpr int kMaxBatchMenu = 8;
 struct ClassParams {
     const ProbDesc *probs;
     int nprob;
+    int whole;        // TSM2L class: groups are whole row blocks (no partial sums)
     int64_t ngroups;  // 0: the class has no work in this launch
     float *ws;        // partial-sum slots: (grid + row blocks) x KC x BM
     int *counters;    // one arrival counter per row block, zero between launches
     int64_t nrb;      // row blocks of the class (counters; slots beyond the grid)
+};
+
+// Shares of the TSM2L classes in the single launch of a batch plan, adapted
+// from launch to launch (plan-owned device memory).  Block b takes the
+// fraction w[b] / sum(w) of every TSM2L class's row blocks; each launch
+// records when every block reached its TSM2L work, when it finished and how
+// many stages it consumed, and the last block to finish sets the weights of
+// the next launch so that all blocks would have finished together.  Whole row
+// blocks are computed the same way whoever owns them, so the results do not
+// depend on the weights.
+constexpr int kBalanceMaxBlocks = 1024;
+struct BatchBalance {
+    int epoch;  // launches completed: weights are read from w[epoch & 1]
+    int done;   // blocks finished in the running launch (zero between launches)
+    int bad;    // a block gave up in the running launch: keep the weights
+    int pad;
+    float w[2][kBalanceMaxBlocks];
+    unsigned long long t_lstart[kBalanceMaxBlocks];  // first TSM2L class reached (ns)
+    unsigned long long t_end[kBalanceMaxBlocks];     // consumers done (ns)
+    long long units[kBalanceMaxBlocks];              // TSM2L stages consumed
 };
 
 struct BatchKParams {
@@ -155,6 +176,7 @@ struct BatchKParams {
     unsigned *status;
     int64_t wait_ns;
     unsigned long long *trace;  // optional: 4 words per block (start, 0, end, 0); nullptr: off
+    BatchBalance *bal;          // adaptive TSM2L shares (single launch); nullptr: equal shares
 };
 
 struct BatchClass {

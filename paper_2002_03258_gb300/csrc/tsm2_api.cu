@@ -624,6 +624,7 @@ struct tsm2_batch_plan_s {
     cudaGraphExec_t graph = nullptr;
     cudaStream_t capture = nullptr;  // private stream the graph is captured on
     double total_bytes = 0;
+    tsm2::BatchBalance *d_bal = nullptr;  // adaptive TSM2L shares of the single launch
 };
 
 namespace tsm2 {
@@ -651,6 +652,7 @@ void destroy_plan(tsm2_batch_plan_s *P) {
     }
     if (P->fork) cudaEventDestroy(P->fork);
     if (P->capture) cudaStreamDestroy(P->capture);
+    if (P->d_bal) cudaFree(P->d_bal);
     cudaSetDevice(cur);
     delete P;
 }
@@ -660,14 +662,17 @@ void destroy_plan(tsm2_batch_plan_s *P) {
 void reset_plan_counters(int dev) {
     std::lock_guard<std::mutex> lk(g_plans_mu);
     for (tsm2_batch_plan_s *P : g_plans)
-        if (P->dev == dev)
+        if (P->dev == dev) {
             for (auto &c : P->classes)
                 if (c.d_ws) cudaMemset(c.d_ws, 0, c.counter_bytes);
+            if (P->d_bal) cudaMemset(P->d_bal, 0, 4 * sizeof(int));  // epoch, done, bad
+        }
 }
 
 void class_params(const tsm2_batch_plan_s::Cls &c, ClassParams &cp) {
     cp.probs = c.d_probs;
     cp.nprob = (int)c.host.size();
+    cp.whole = c.cls->op == 'w' ? 1 : 0;
     cp.ngroups = c.ngroups;
     cp.counters = static_cast<int *>(c.d_ws);
     cp.ws = reinterpret_cast<float *>(static_cast<char *>(c.d_ws) + c.counter_bytes);
@@ -675,8 +680,9 @@ void class_params(const tsm2_batch_plan_s::Cls &c, ClassParams &cp) {
 }
 
 // One launch of the plan's batch kernel over the classes [lo, hi) (all
-// other slots empty) on `grid` blocks.
-tsm2_status launch_classes(tsm2_batch_plan_s *P, int lo, int hi, int grid, cudaStream_t stream) {
+// other slots empty) on `grid` blocks; `adapt`: TSM2L shares from the plan's
+// adaptive weights.
+tsm2_status launch_classes(tsm2_batch_plan_s *P, int lo, int hi, int grid, cudaStream_t stream, bool adapt = false) {
     DeviceState *dev = nullptr;
     tsm2_status st = device_state(&dev);
     if (st != TSM2_SUCCESS) return st;
@@ -686,6 +692,7 @@ tsm2_status launch_classes(tsm2_batch_plan_s *P, int lo, int hi, int grid, cudaS
     kp.status = dev->status;
     kp.wait_ns = g_wait_ns;
     kp.trace = (g_trace && g_trace_blocks >= grid) ? g_trace : nullptr;
+    kp.bal = (adapt && g_balance == 0 && grid <= kBalanceMaxBlocks) ? P->d_bal : nullptr;
     const cudaError_t e = P->menu->launch(kp, grid < 1 ? 1 : grid, stream);
     return e == cudaSuccess ? TSM2_SUCCESS : cuda_error(e, "batch kernel launch");
 }
@@ -703,7 +710,7 @@ tsm2_status plan_execute(tsm2_batch_plan_s *P, cudaStream_t stream, int only) {
         if (e != cudaSuccess) return cuda_error(e, "cudaMemset2DAsync");
     }
     if (nc == 0) return TSM2_SUCCESS;
-    if (P->mode == TSM2_BATCH_SINGLE_LAUNCH) return launch_classes(P, 0, nc, P->single_grid, stream);
+    if (P->mode == TSM2_BATCH_SINGLE_LAUNCH) return launch_classes(P, 0, nc, P->single_grid, stream, true);
     if (P->mode == TSM2_BATCH_SERIAL) {
         for (int i = 0; i < nc; ++i) {
             tsm2_status s = launch_classes(P, i, i + 1, class_grid_alone(P, i), stream);
@@ -1422,6 +1429,14 @@ tsm2_status tsm2_batch_plan_create_s(int nprob, const tsm2_problem_s *probs, int
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        // Even shares for the first single launch.
+        std::vector<BatchBalance> init(1);
+        std::memset(init.data(), 0, sizeof(BatchBalance));
+        for (int b = 0; b < kBalanceMaxBlocks; ++b) init[0].w[0][b] = init[0].w[1][b] = 1.0f;
+        e = cudaMalloc(&P->d_bal, sizeof(BatchBalance));
+        if (e == cudaSuccess) e = cudaMemcpy(P->d_bal, init.data(), sizeof(BatchBalance), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         destroy_plan(P);
         return cuda_error(e, "tsm2_batch_plan_create_s");

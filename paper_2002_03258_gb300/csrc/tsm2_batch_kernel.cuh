@@ -61,7 +61,10 @@ struct BatchLayout {
     // full, empty and meta barriers (STAGES each), then the stage records
     static constexpr size_t OFF_META = OFF_BAR + 3 * STAGES * sizeof(uint64_t);
     static constexpr size_t OFF_FLAGS = OFF_META + STAGES * 32;
-    static constexpr size_t SMEM = OFF_FLAGS + 32 + 128;  // + slack for 128-byte alignment
+    // This block's weighted share of the TSM2L classes: Q below, Q below +
+    // own, Q total (0: equal shares), launch epoch.
+    static constexpr size_t OFF_WSH = OFF_FLAGS + 32;
+    static constexpr size_t SMEM = OFF_WSH + 32 + 128;  // + slack for 128-byte alignment
     static_assert(SMEM <= 227 * 1024, "shared memory per block");
 };
 
@@ -82,8 +85,19 @@ static_assert(sizeof(StageMeta) == 32, "stage record size");
 // Gc = min(grid, NG).  With more blocks than groups only the first NG blocks
 // take one group each, so every block between the first and last owner of a
 // split row block has written its partial sum (the fix-up adds them all).
-__device__ __forceinline__ bool class_share(const ClassParams &cp, int64_t &Gc, int64_t &gs, int64_t &ge) {
+// TSM2L classes (whole row blocks) with adaptive weights (wsh[2] > 0): groups
+// [NG*Qb/Qt, NG*(Qb+Qg)/Qt), where Qb is the sum of the integer weights of the
+// blocks before g; every block computes the same integer prefix sums, so the
+// shares tile the class exactly.
+__device__ __forceinline__ bool class_share(const ClassParams &cp, const int64_t *wsh, int64_t &Gc, int64_t &gs,
+                                            int64_t &ge) {
     const int64_t G = gridDim.x, g = blockIdx.x;
+    if (cp.whole && wsh[2] > 0) {
+        Gc = G;
+        gs = cp.ngroups * wsh[0] / wsh[2];
+        ge = cp.ngroups * wsh[1] / wsh[2];
+        return gs < ge;
+    }
     Gc = G < cp.ngroups ? G : cp.ngroups;
     if (g >= Gc) return false;
     gs = g * cp.ngroups / Gc;
@@ -159,7 +173,7 @@ __device__ __forceinline__ void produce_class(const ClassParams &cp, int cls, un
                                               const BatchKParams &p, Ring &ring, uint32_t &issued,
                                               uint32_t &last_par, bool &stop, uint64_t policy) {
     int64_t Gc, gs, ge;
-    if (stop || !class_share(cp, Gc, gs, ge)) return;
+    if (stop || !class_share(cp, reinterpret_cast<const int64_t *>(smem + LY::OFF_WSH), Gc, gs, ge)) return;
     Walk w;
     w.start(cp, gs);
     for (int64_t gg = gs; gg < ge && !stop; ++gg) {
@@ -196,9 +210,9 @@ __device__ __forceinline__ void produce_class(const ClassParams &cp, int cls, un
 }
 
 // Stages a block runs in one class: whole groups of gran stages each.
-__device__ __forceinline__ int64_t class_units(const ClassParams &cp) {
+__device__ __forceinline__ int64_t class_units(const ClassParams &cp, const int64_t *wsh) {
     int64_t Gc, gs, ge;
-    if (!class_share(cp, Gc, gs, ge)) return 0;
+    if (!class_share(cp, wsh, Gc, gs, ge)) return 0;
     int64_t units = 0;
     for (int pi = find_problem(cp.probs, cp.nprob, gs); pi < cp.nprob; ++pi) {
         const ProbDesc &d = cp.probs[pi];
@@ -227,7 +241,8 @@ __device__ __forceinline__ void loader_warp(const BatchKParams &p, unsigned char
                                             uint64_t *metab, volatile int *flags, int w, int lane) {
     int total = 0;  // a block's stages: far below 2^31
     int ci = 0;
-    ((total += (int)class_units(p.cls[ci++]), (void)sizeof(Ks)), ...);
+    const int64_t *wsh = reinterpret_cast<const int64_t *>(smem + LY::OFF_WSH);
+    ((total += (int)class_units(p.cls[ci++], wsh), (void)sizeof(Ks)), ...);
     int s = w, ph = 0;  // stage and parity of unit u, stepped by 3
     for (int u = w; u < total; u += 3) {
         bool ok = !flags[0] && mbar_wait_bounded(&metab[s], (uint32_t)ph, p.wait_ns, flags);
@@ -258,11 +273,16 @@ __device__ __forceinline__ void loader_warp(const BatchKParams &p, unsigned char
 template <class K, class LY>
 __device__ __forceinline__ void consume_class(const ClassParams &cp, unsigned char *smem, uint64_t *full,
                                               uint64_t *empty, volatile int *flags, const BatchKParams &p,
-                                              Ring &ring, bool &aborted) {
+                                              Ring &ring, bool &aborted, unsigned long long &lstart,
+                                              long long &lunits) {
     using T = float;
     using vec_t = typename K::vec_t;
+    if constexpr (K::BRES) {
+        if (p.bal && lstart == 0) lstart = globaltimer_ns();  // the block reached its TSM2L work
+    }
     int64_t G, gs, ge;  // G: the blocks that share this class
-    if (!class_share(cp, G, gs, ge)) return;
+    if (!class_share(cp, reinterpret_cast<const int64_t *>(smem + LY::OFF_WSH), G, gs, ge)) return;
+    if constexpr (K::BRES) lunits += class_units(cp, reinterpret_cast<const int64_t *>(smem + LY::OFF_WSH));
     const int64_t g = blockIdx.x;
     T *sBres = reinterpret_cast<T *>(smem + LY::OFF_BRES);
     T *sRed = reinterpret_cast<T *>(smem + LY::OFF_RED);
@@ -486,6 +506,116 @@ __device__ __forceinline__ void consume_class(const ClassParams &cp, unsigned ch
     }
 }
 
+// Integer share weight of a block (2^16 = an even share), from the float
+// weight the previous launch left; bounded to [1/16, 16] of an even share.
+__device__ __forceinline__ long long weight_q(float x) {
+    if (!(x >= 0.0625f)) x = (x > 0.0f) ? 0.0625f : 1.0f;  // also NaN -> even share
+    if (x > 16.0f) x = 16.0f;
+    return (long long)(x * 65536.0f + 0.5f);
+}
+
+// Warp 1 of every block at launch: this block's share of the TSM2L classes
+// from the weights of the running epoch (integer prefix sums, the same in
+// every block).
+__device__ __forceinline__ void balance_shares(const BatchKParams &p, int64_t *wsh, int lane) {
+    const int G = gridDim.x, g = blockIdx.x;
+    if (!p.bal || G > kBalanceMaxBlocks) {
+        if (lane == 0) wsh[0] = wsh[1] = wsh[2] = wsh[3] = 0;
+        return;
+    }
+    const int e = __ldcg(&p.bal->epoch);
+    const float *w = p.bal->w[e & 1];
+    long long below = 0, mine = 0, all = 0;
+    for (int b = lane; b < G; b += 32) {
+        const long long q = weight_q(__ldcg(&w[b]));
+        all += q;
+        if (b < g) below += q;
+        if (b == g) mine = q;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        below += __shfl_xor_sync(0xffffffffu, below, o);
+        mine += __shfl_xor_sync(0xffffffffu, mine, o);
+        all += __shfl_xor_sync(0xffffffffu, all, o);
+    }
+    if (lane == 0) {
+        wsh[0] = below;
+        wsh[1] = below + mine;
+        wsh[2] = all;
+        wsh[3] = e;
+    }
+}
+
+// The last block of a launch: weights for the next one.  Block b ran its
+// TSM2L stages u_b at rate r_b = u_b / (end_b - start_b) from start_b; all
+// blocks finish together at T if block b gets r_b (T - start_b) stages, with
+// T fixed by the total.  The new weight is half the old (normalised) and half
+// that target; blocks without TSM2L work count at the mean rate.  Warp 4's
+// 32 lanes share the blocks.
+__device__ __forceinline__ void balance_update(BatchBalance *bal, int e, int lane) {
+    const int G = gridDim.x;
+    const float *wo = bal->w[e & 1];
+    float *wn = bal->w[(e + 1) & 1];
+    unsigned long long l0 = ~0ull;
+    double U = 0, rs = 0, nv = 0;
+    for (int b = lane; b < G; b += 32) {
+        const unsigned long long ls = __ldcg(&bal->t_lstart[b]), te = __ldcg(&bal->t_end[b]);
+        const long long u = __ldcg(&bal->units[b]);
+        l0 = ls < l0 ? ls : l0;
+        U += (double)u;
+        if (u > 0 && te > ls) {
+            rs += (double)u / (double)(te - ls);
+            nv += 1;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long x = __shfl_xor_sync(0xffffffffu, l0, o);
+        l0 = x < l0 ? x : l0;
+        U += __shfl_xor_sync(0xffffffffu, U, o);
+        rs += __shfl_xor_sync(0xffffffffu, rs, o);
+        nv += __shfl_xor_sync(0xffffffffu, nv, o);
+    }
+    const bool keep = __ldcg(&bal->bad) != 0 || U <= 0 || nv <= 0;
+    const double rmean = nv > 0 ? rs / nv : 1.0;
+    auto rate = [&](int b) {
+        const unsigned long long ls = __ldcg(&bal->t_lstart[b]), te = __ldcg(&bal->t_end[b]);
+        const long long u = __ldcg(&bal->units[b]);
+        return (u > 0 && te > ls) ? (double)u / (double)(te - ls) : rmean;
+    };
+    double R = 0, RL = 0, W = 0;
+    for (int b = lane; b < G; b += 32) {
+        const double r = rate(b);
+        R += r;
+        RL += r * (double)(__ldcg(&bal->t_lstart[b]) - l0);
+        W += (double)weight_q(__ldcg(&wo[b]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        R += __shfl_xor_sync(0xffffffffu, R, o);
+        RL += __shfl_xor_sync(0xffffffffu, RL, o);
+        W += __shfl_xor_sync(0xffffffffu, W, o);
+    }
+    const double Tend = (U + RL) / R;  // common end time (ns after the earliest start)
+    const double floor_u = 0.02 * U / G;
+    double S = 0;
+    for (int b = lane; b < G; b += 32) {
+        const double t = rate(b) * (Tend - (double)(__ldcg(&bal->t_lstart[b]) - l0));
+        S += t > floor_u ? t : floor_u;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+    for (int b = lane; b < G; b += 32) {
+        const double old = (double)weight_q(__ldcg(&wo[b])) * G / W;  // mean 1
+        double x = old;
+        if (!keep) {
+            const double t = rate(b) * (Tend - (double)(__ldcg(&bal->t_lstart[b]) - l0));
+            x = 0.5 * old + 0.5 * (t > floor_u ? t : floor_u) * G / S;
+        }
+        wn[b] = (float)x;
+    }
+}
+
 // Register split of the batch kernel: the producer warpgroup (producer lane
 // and loader warps) gets PREG registers per thread, the consumers the rest of
 // the launch pool (384 x 168), rounded down to the multiple of 8 that
@@ -512,6 +642,7 @@ __global__ void __launch_bounds__(384, 1) batch_kernel(const __grid_constant__ B
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
 
+    if (warp == 1) balance_shares(p, reinterpret_cast<int64_t *>(smem + LY::OFF_WSH), lane);
     if (threadIdx.x == 0) {
         if (p.trace) p.trace[4 * blockIdx.x] = globaltimer_ns();
         for (int s = 0; s < LY::STAGES; ++s) {
@@ -551,9 +682,39 @@ __global__ void __launch_bounds__(384, 1) batch_kernel(const __grid_constant__ B
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(RG::C));
     Ring ring;
     bool aborted = false;
+    unsigned long long lstart = 0;
+    long long lunits = 0;
     int ci = 0;
-    (consume_class<Ks, LY>(p.cls[ci++], smem, full, empty, flags, p, ring, aborted), ...);
-    if (p.trace && threadIdx.x == 128) p.trace[4 * blockIdx.x + 2] = globaltimer_ns();
+    (consume_class<Ks, LY>(p.cls[ci++], smem, full, empty, flags, p, ring, aborted, lstart, lunits), ...);
+    const unsigned long long t_end = globaltimer_ns();
+    if (p.trace && threadIdx.x == 128) p.trace[4 * blockIdx.x + 2] = t_end;
+    if (p.bal && gridDim.x <= kBalanceMaxBlocks) {
+        // Record this block's TSM2L timing; the last block to get here sets
+        // the next launch's weights and rearms the counters.
+        const int64_t *wsh = reinterpret_cast<const int64_t *>(smem + LY::OFF_WSH);
+        named_bar_sync(1, 256);  // every consumer warp is done (flags[1] is free again)
+        if (threadIdx.x == 128) {
+            const int g = blockIdx.x;
+            p.bal->t_lstart[g] = lstart ? lstart : t_end;
+            p.bal->t_end[g] = t_end;
+            p.bal->units[g] = lunits;
+            if (flags[0]) atomicExch(&p.bal->bad, 1);
+            __threadfence();
+            flags[1] = atomicAdd(&p.bal->done, 1) == (int)gridDim.x - 1;
+        }
+        named_bar_sync(1, 256);
+        if (flags[1] && warp == 4) {
+            __threadfence();
+            balance_update(p.bal, (int)wsh[3], lane);
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                p.bal->bad = 0;
+                p.bal->done = 0;
+                p.bal->epoch = (int)wsh[3] + 1;
+            }
+        }
+    }
 }
 
 template <int PREG, class... Ks>

@@ -243,3 +243,40 @@ def test_class_with_fewer_groups_than_blocks(mode):
         assert pkg.tsm2_get_device_status(0) == 0
         check_all(items)
         plan.close()
+
+
+def test_adaptive_tsm2l_shares_keep_the_bits():
+    """The single launch moves TSM2L row blocks between blocks from launch to
+    launch (weights adapted to each block's measured rate); whole row blocks
+    are computed alike whoever owns them, so every launch, the graph replay
+    and the equal-share launch give the same bits."""
+    import paper_2002_03258_gb300 as pkg
+    import paper_2002_03258_gb300.batched as bt
+    items = make_batch(seed=11)
+    plan = bt.BatchPlan([it["p"] for it in items], bt.variant_flag(1))
+    try:
+        plan.execute(0)
+        assert pkg.tsm2_get_device_status(0) == 0
+        check_all(items)
+        first = [it["tC"].clone() for it in items]
+        for r in range(6):
+            for it in items:
+                it["tC"].fill_(float("nan"))
+            if r % 2:
+                plan.graph_launch(0)
+            else:
+                plan.execute(0)
+            torch.cuda.synchronize()
+            assert pkg.tsm2_get_device_status(0) == 0
+            for a, it in zip(first, items):
+                assert torch.equal(torch.nan_to_num(a, 7.0), torch.nan_to_num(it["tC"], 7.0)), f"launch {r}"
+        pkg.tsm2_set_balance(1)  # equal shares
+        for it in items:
+            it["tC"].fill_(float("nan"))
+        plan.execute(0)
+        torch.cuda.synchronize()
+        for a, it in zip(first, items):
+            assert torch.equal(torch.nan_to_num(a, 7.0), torch.nan_to_num(it["tC"], 7.0))
+    finally:
+        pkg.tsm2_set_balance(0)
+        plan.close()
