@@ -25,7 +25,10 @@
 //    persistent, one thread block per SM.  The work units (one pipeline
 //    stage each, i.e. a BM x BNS tile of A) are numbered row block by row
 //    block and every block takes a contiguous run of them, so all blocks get
-//    the same amount of work whatever the shape.
+//    the same amount of work whatever the shape.  With B resident (TSM2L),
+//    whole row blocks are instead handed out at run time: each block starts
+//    with its own and then claims the next from a counter, so blocks on SMs
+//    that stream faster take more.
 //  * When a block's run starts or ends inside a row block (TSM2R schedule),
 //    its partial sums go to a workspace slot; the last block to finish a row
 //    block (an atomic arrival counter, no waiting) adds the slots in a fixed
