@@ -268,8 +268,9 @@ tsm2_status tsm2r_s_noalloc(int64_t m, int64_t n, int64_t k,
  * 3.2.2) come in compiled variants (pipeline stages, rows of C per lane,
  * inner columns per warp and stage), chosen per plan.  Execution modes:
  *  - TSM2_BATCH_SINGLE_LAUNCH (default): ONE persistent kernel whose blocks
- *    walk their share of every class in turn, through one pipeline.  The
- *    shares of the TSM2L classes adapt from launch to launch: each launch
+ *    walk their share of every class in turn, through one pipeline.  In
+ *    plans of 16 GB or more (algorithmic bytes) the shares of the TSM2L
+ *    classes adapt from launch to launch: each launch
  *    records every block's TSM2L rate and start, and the last block to
  *    finish sets the next launch's shares so that all blocks would finish
  *    together (TSM2L row blocks are computed whole, so the bits do not
@@ -406,10 +407,11 @@ void tsm2_set_grid(int blocks);
  * at run time from an atomic counter, each block starting with its own
  * (default: blocks on SMs that stream faster take more row blocks), and in
  * the single launch of a batch plan shares adapted from launch to launch;
- * 1 = a static partition, equal contiguous runs of row blocks.  Every row
- * block is computed whole by one thread block in the same order either way,
- * so the results are bitwise equal.  TSM2R and TSM2L with staged B (n > 64)
- * always use their static partitions. */
+ * 1 = a static partition, equal contiguous runs of row blocks; 2 = as 0,
+ * with batch plans of any size adapting their shares (for tests).  Every
+ * row block is computed whole by one thread block in the same order either
+ * way, so the results are bitwise equal.  TSM2R and TSM2L with staged B
+ * (n > 64) always use their static partitions. */
 void tsm2_set_balance(int mode);
 
 /* How the host-operand entry points move page-locked buffers: 0 = copy

@@ -31,7 +31,7 @@ int64_t g_wait_ns = 1000000000LL;
 int g_path = 0;
 int g_grid_override = 0;
 int g_host_copy = 0;               // 0: SM copies for device-mapped page-locked host buffers; 1: copy engines
-int g_balance = 0;                 // 0: TSM2L row blocks claimed at run time; 1: static partition
+int g_balance = 0;                 // 0: TSM2L row blocks claimed at run time; 1: static; 2: 0 + batched shares always adapted
 thread_local int t_grid_cap = 0;   // > 0: upper bound of the product kernels' persistent grid (this thread)
 unsigned long long *g_trace = nullptr;
 int64_t g_trace_blocks = 0;
@@ -679,6 +679,13 @@ void class_params(const tsm2_batch_plan_s::Cls &c, ClassParams &cp) {
     cp.nrb = c.nrb;
 }
 
+// Adaptive TSM2L shares pay off when the TSM2L phase is long against the
+// launch-to-launch noise of when blocks reach it.  Measured on GB300 (one
+// launch, median of 15): the 512-problem batch (42.8 GB) 1.4-2.2% faster,
+// its first 120 problems (9.3 GB) 0.4-1% slower, its first 40 (3.4 GB) 5%
+// slower.  Plans below this size keep equal shares.
+constexpr double kAdaptMinBytes = 16e9;
+
 // One launch of the plan's batch kernel over the classes [lo, hi) (all
 // other slots empty) on `grid` blocks; `adapt`: TSM2L shares from the plan's
 // adaptive weights.
@@ -692,7 +699,7 @@ tsm2_status launch_classes(tsm2_batch_plan_s *P, int lo, int hi, int grid, cudaS
     kp.status = dev->status;
     kp.wait_ns = g_wait_ns;
     kp.trace = (g_trace && g_trace_blocks >= grid) ? g_trace : nullptr;
-    kp.bal = (adapt && g_balance == 0 && grid <= kBalanceMaxBlocks) ? P->d_bal : nullptr;
+    kp.bal = (adapt && g_balance != 1 && grid <= kBalanceMaxBlocks) ? P->d_bal : nullptr;
     const cudaError_t e = P->menu->launch(kp, grid < 1 ? 1 : grid, stream);
     return e == cudaSuccess ? TSM2_SUCCESS : cuda_error(e, "batch kernel launch");
 }
@@ -710,7 +717,8 @@ tsm2_status plan_execute(tsm2_batch_plan_s *P, cudaStream_t stream, int only) {
         if (e != cudaSuccess) return cuda_error(e, "cudaMemset2DAsync");
     }
     if (nc == 0) return TSM2_SUCCESS;
-    if (P->mode == TSM2_BATCH_SINGLE_LAUNCH) return launch_classes(P, 0, nc, P->single_grid, stream, true);
+    if (P->mode == TSM2_BATCH_SINGLE_LAUNCH)
+        return launch_classes(P, 0, nc, P->single_grid, stream, g_balance == 2 || P->total_bytes >= kAdaptMinBytes);
     if (P->mode == TSM2_BATCH_SERIAL) {
         for (int i = 0; i < nc; ++i) {
             tsm2_status s = launch_classes(P, i, i + 1, class_grid_alone(P, i), stream);
@@ -1585,7 +1593,7 @@ void tsm2_set_grid(int blocks) { g_grid_override = blocks < 0 ? 0 : blocks; }
 
 void tsm2_set_host_copy(int mode) { g_host_copy = mode == 1 ? 1 : 0; }
 
-void tsm2_set_balance(int mode) { g_balance = mode == 1 ? 1 : 0; }
+void tsm2_set_balance(int mode) { g_balance = (mode == 1 || mode == 2) ? mode : 0; }
 
 void tsm2_set_trace(unsigned long long *device_words, int64_t blocks) {
     g_trace = device_words;

@@ -254,6 +254,7 @@ def test_adaptive_tsm2l_shares_keep_the_bits():
     import paper_2002_03258_gb300.batched as bt
     items = make_batch(seed=11)
     plan = bt.BatchPlan([it["p"] for it in items], bt.variant_flag(1))
+    pkg.tsm2_set_balance(2)  # adapt although the plan is small
     try:
         plan.execute(0)
         assert pkg.tsm2_get_device_status(0) == 0
@@ -271,6 +272,8 @@ def test_adaptive_tsm2l_shares_keep_the_bits():
             for a, it in zip(first, items):
                 assert torch.equal(torch.nan_to_num(a, 7.0), torch.nan_to_num(it["tC"], 7.0)), f"launch {r}"
         pkg.tsm2_set_balance(1)  # equal shares
+        plan.close()
+        plan = bt.BatchPlan([it["p"] for it in items], bt.variant_flag(1))  # a fresh graph
         for it in items:
             it["tC"].fill_(float("nan"))
         plan.execute(0)
