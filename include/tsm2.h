@@ -262,7 +262,8 @@ tsm2_status tsm2r_s_noalloc(int64_t m, int64_t n, int64_t k,
  * TSM2R with 8, 12 or 16 columns, TSM2L with 8, 16, 24 or 32; each column chunk
  * goes to the narrowest class that holds it).  In every class the work units
  * of all its problems are numbered end to end and every block of a persistent
- * grid takes an equal, contiguous share, crossing problem boundaries
+ * grid takes a contiguous share (equal; weighted for the TSM2L classes of
+ * large plans, below), crossing problem boundaries
  * (Algorithm 5's persistent walk over tiles, Sec. 3.2.2, extended across
  * problems).  The tile parameters that the paper tunes offline (Sec. 3.1.9,
  * 3.2.2) come in compiled variants (pipeline stages, rows of C per lane,
