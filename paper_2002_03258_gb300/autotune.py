@@ -38,6 +38,9 @@ WIDEST = {"r": 16, "l": 32}  # widest TSM2R / TSM2L class of every variant
 # Assumed DRAM round-trip latency (SM cycles) for the Little's-law estimate;
 # the paper leaves it a platform constant (Sec. 3.1.8).
 LATENCY_CYCLES = 1000.0
+# Latency (SM cycles) of a dependent FMA, for the model's compute
+# utilisation in Algorithm 7 (reported only).
+FMA_LATENCY_CYCLES = 4.0
 # Fraction of the binary32 FMA peak the kernels sustain at their on-chip
 # limit (ncu: 65-69% FMA-pipe activity for TSM2R k = 16 and TSM2L
 # n = k = 32).  The paper's threshold assumes the full peak; the seed uses
@@ -152,6 +155,18 @@ def device_model(torch, dev, hbm_gbs=None, fp32_gflops=None) -> perfmodel.Gpu:
     return perfmodel.Gpu(props.name, peak, hbm_gbs or 8000.0, sms=sms, clock_ghz=clock_ghz)
 
 
+def alg7_record(gpu: perfmodel.Gpu, ks=(2, 8, 16, 32)):
+    """Algorithm 7's (t2, t3) for binary32 TSM2R with an 8192 x 8192 A on
+    this GPU, for several skinny widths: what the paper's procedure would
+    pick for a thread-per-row kernel, reported beside the measured choice
+    (the library's tiles are compiled variants, chosen by measurement)."""
+    out = {}
+    for k in ks:
+        c = perfmodel.optimize_tiles(gpu, 8192, 8192, k, 4, LATENCY_CYCLES, FMA_LATENCY_CYCLES)
+        out[f"k{k}"] = {"t2": c.t2, "t3": c.t3, "bound": c.bound, "model_ms": round(c.time_s * 1e3, 4)}
+    return out
+
+
 def make_plan(problems, variant, flags, mode):
     plan = BatchPlan(problems, flags | variant_flag(variant))
     plan.set_mode(mode)
@@ -204,7 +219,8 @@ def autotune(problems, reps=3, flush=None, cache_path=None, log=None, hbm_gbs=No
                gpu.bw_gbs, gpu.sms, gpu.clock_ghz, LATENCY_CYCLES)), "t2_threshold_fp32": round(
                perfmodel.t2_threshold(gpu.peak_gflops, gpu.bw_gbs, 4), 2), "t2_threshold_fp32_sustained": round(
                perfmodel.t2_threshold(gpu.peak_gflops * FMA_SUSTAINED, gpu.bw_gbs, 4), 2),
-               "fma_sustained": FMA_SUSTAINED, "latency_cycles": LATENCY_CYCLES},
+               "fma_sustained": FMA_SUSTAINED, "latency_cycles": LATENCY_CYCLES,
+               "alg7_tsm2r_8192": alg7_record(gpu)},
            "trials": trials}
     if cache_path:
         store_cache(cache_path, key, {k: rec[k] for k in ("variant", "flags", "mode", "ms", "launches")})

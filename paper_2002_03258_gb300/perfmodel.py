@@ -6,6 +6,11 @@ at a time (``tile_size_C``), t3 the number of A elements fetched at a time
 (``tile_size_A``), ``bytes`` the element size.  Peak performance is in
 GFLOP/s and bandwidth in GB/s, as in the paper's platform table.
 
+Algorithm 7 itself (``optimize_tiles``: t2 and t3 by gradient descent on
+the model's time) is restated for reference and reported beside the tuner's
+measurements; the library's kernels have no per-thread t2/t3 (their tiles
+are compiled variants), so measurement picks among those.
+
 Two parts feed the library's batched tuner (``autotune.seed_candidate``):
 the Little's-law estimate of bytes in flight per SM picks the seed tile
 variant (the pipeline must keep that much of A in flight), and the
@@ -79,6 +84,15 @@ def util_mem(gpu: Gpu, t2: int, t3: int, bytes_per_elem: int, latency_cycles: fl
     return min(1.0, conc / need)
 
 
+def util_comp(gpu: Gpu, t2: float, t3: float, bytes_per_elem: int, latency_cycles: float, c_setup: int = 0) -> float:
+    """Little's-law estimate of compute utilisation (Sec. 3.1.8):
+    Concurrent_comp = MaxOccup * t3 * t2 operations in flight per SM against
+    Concurrent_max_comp = latency_comp * PeakPerf / (#SM * clock)."""
+    conc = max_occupancy(gpu, t2, t3, bytes_per_elem, c_setup) * t3 * t2
+    need = latency_cycles * (gpu.peak_gflops * 1e9) / (gpu.sms * gpu.clock_ghz * 1e9)
+    return min(1.0, conc / need)
+
+
 def bytes_in_flight_per_sm(bw_gbs: float, sms: int, clock_ghz: float, latency_cycles: float) -> float:
     """Concurrent_max_mem in bytes: what each SM must keep in flight to reach
     the bandwidth peak.  Used to size the shared-memory ring."""
@@ -95,3 +109,107 @@ PAPER_GPUS_DOUBLE = {
     # Sec. 4.2.5: the A100 figures used for the paper's prediction.
     "A100": Gpu("A100", 9700.0, 1555.0),
 }
+
+
+# ---- Algorithm 7: choosing t2 and t3 from the model --------------------------
+
+@dataclass(frozen=True)
+class TileChoice:
+    t2: int
+    t3: int
+    bound: str        # "memory" or "compute": the objective the choice minimised
+    time_s: float     # the model's time at the rounded (t2, t3)
+
+
+def mem_time(gpu: Gpu, m: int, n: int, k: int, t2: float, t3: float, bytes_per_elem: int, latency_mem: float,
+             c_setup: int = 0) -> float:
+    """Model time of the memory-bound case: A (m x n, n the reduced
+    dimension) is read ceil-free k / t2 times (one pass per t2 columns of C,
+    the paper's m k n / t2 with its names), at PeakBand * Util_mem."""
+    total = m * n * (k / t2) * bytes_per_elem
+    return total / (gpu.bw_gbs * 1e9 * max(util_mem(gpu, t2, t3, bytes_per_elem, latency_mem), 1e-12))
+
+
+def comp_time(gpu: Gpu, m: int, n: int, k: int, t2: float, t3: float, bytes_per_elem: int, latency_comp: float,
+              c_setup: int = 0) -> float:
+    """Model time of the compute-bound case: 2 m n k operations at
+    PeakPerf * Util_comp."""
+    flops = 2.0 * m * n * k
+    u = util_comp(gpu, t2, t3, bytes_per_elem, latency_comp, c_setup)
+    return flops / (gpu.peak_gflops * 1e9 * max(u, 1e-12))
+
+
+def _descend(f, lo2: float, hi2: float, lo3: float, hi3: float, step: float, stop: float, max_iter: int):
+    """Projected gradient descent on f(t2, t3) / f(start) from (lo2, lo3)
+    (the paper's start (1, 1), clipped into the box): central differences,
+    steps of `step` x gradient, clipped back into the box, until a step moves
+    less than `stop`."""
+    x2, x3 = min(max(1.0, lo2), hi2), min(max(1.0, lo3), hi3)
+    f0 = f(x2, x3)
+    g = (lambda a, b: f(a, b) / f0) if f0 > 0 else f
+    h = 1e-3
+
+    def slope(fa, a_lo, a_hi):
+        # central difference inside the box, one-sided at its faces, 0 when
+        # the box is a single point along this axis
+        return (fa(a_hi) - fa(a_lo)) / (a_hi - a_lo) if a_hi > a_lo else 0.0
+
+    for _ in range(max_iter):
+        d2 = slope(lambda a: g(a, x3), max(x2 - h, lo2), min(x2 + h, hi2))
+        d3 = slope(lambda b: g(x2, b), max(x3 - h, lo3), min(x3 + h, hi3))
+        n2 = min(max(x2 - step * d2, lo2), hi2)
+        n3 = min(max(x3 - step * d3, lo3), hi3)
+        moved = abs(n2 - x2) + abs(n3 - x3)
+        x2, x3 = n2, n3
+        if moved < stop:
+            break
+    return x2, x3
+
+
+def optimize_tiles(gpu: Gpu, m: int, n: int, k: int, bytes_per_elem: int, latency_mem: float, latency_comp: float,
+                   c_setup: int = 0, t3_max: float = 64.0, step: float = 0.1, stop: float = 1e-4,
+                   max_iter: int = 200000) -> TileChoice:
+    """Algorithm 7 (Sec. 3.1.9): the (t2, t3) that minimise the model's time
+    for C (m x k) = A (m x n) B (n x k), k the skinny width.
+
+    If k <= t2_threshold the problem is memory-bound and the memory time is
+    minimised over 1 <= t2 <= k.  Otherwise the compute time is minimised
+    over t2_threshold <= t2 <= k and the memory time over 1 <= t2 <=
+    t2_threshold, and the faster of the two choices is kept.  Gradient
+    descent from (1, 1) with step 0.1 and stop threshold 1e-4, then rounding
+    to the nearest integers, as the paper states; t3 >= 1 with an upper bound
+    t3_max (the model alone would let t3 grow without limit once occupancy
+    no longer depends on it)."""
+    thr = t2_threshold(gpu.peak_gflops, gpu.bw_gbs, bytes_per_elem)
+
+    def tm(a, b):
+        return mem_time(gpu, m, n, k, a, b, bytes_per_elem, latency_mem, c_setup)
+
+    def tc(a, b):
+        return comp_time(gpu, m, n, k, a, b, bytes_per_elem, latency_comp, c_setup)
+
+    def rounded(x2, x3, lo2, hi2):
+        return int(min(max(round(x2), lo2), hi2)), int(min(max(round(x3), 1), t3_max))
+
+    if k <= thr:
+        x2, x3 = _descend(tm, 1.0, float(k), 1.0, t3_max, step, stop, max_iter)
+        r2, r3 = rounded(x2, x3, 1, k)
+        return TileChoice(r2, r3, "memory", max(tm(r2, r3), tc(r2, r3)))
+    lo = min(max(1.0, thr), float(k))
+    a2, a3 = _descend(tc, lo, float(k), 1.0, t3_max, step, stop, max_iter)
+    ca = rounded(a2, a3, int(round(lo)), k)
+    b2, b3 = _descend(tm, 1.0, max(1.0, min(thr, float(k))), 1.0, t3_max, step, stop, max_iter)
+    cb = rounded(b2, b3, 1, max(1, int(min(thr, k))))
+    # The two choices are compared on the time of the whole computation, the
+    # larger of its memory and compute times, and the memory-bound choice
+    # replaces the compute-bound one only when it is strictly faster
+    # (readings: the printed algorithm compares the memory objective alone,
+    # which leaves out that the 2 m n k operations take their time whatever t2
+    # is and would then not favour computing on M40 at k = 16, as the paper
+    # reports its procedure did; the text keeps the compute choice unless the
+    # memory one "delivers better performance").
+    t1 = max(tc(*ca), tm(*ca))
+    t2 = max(tc(*cb), tm(*cb))
+    if t2 < t1:
+        return TileChoice(cb[0], cb[1], "memory", t2)
+    return TileChoice(ca[0], ca[1], "compute", t1)

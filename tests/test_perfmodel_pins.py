@@ -53,3 +53,60 @@ def test_register_and_occupancy_formulas():
     assert pm.smem_per_thread(16, 8) == 128
     g = pm.Gpu("x", 1.0, 1.0, sms=1, clock_ghz=1.0, regs_per_sm=65536, smem_per_sm=98304, hw_max_threads=2048)
     assert pm.max_occupancy(g, 16, 4, 8) == min(2048, 65536 / 112, 98304 / 128)
+
+
+# ---- Algorithm 7 (parameter optimisation) -------------------------------------------
+# The paper's platform constants beyond its table (SM count, clock, registers
+# and shared memory per SM) are the GPUs' published figures; the latency
+# constants it profiled are not printed, so the pins hold across a range.
+K40C = pm.Gpu("K40c", 1430.0, 288.0, sms=15, clock_ghz=0.745, regs_per_sm=65536, smem_per_sm=49152,
+              hw_max_threads=2048)
+M40 = pm.Gpu("M40", 213.0, 288.0, sms=24, clock_ghz=0.948, regs_per_sm=65536, smem_per_sm=98304, hw_max_threads=2048)
+
+
+@pytest.mark.parametrize("latency_mem", [200, 400, 800])
+@pytest.mark.parametrize("c_setup", [0, 16, 32])
+def test_alg7_k40c_memory_bound_takes_every_column(latency_mem, c_setup):
+    # Sec. 4.2.1: on K40c every n in 2..16 is memory-bound and the procedure
+    # printed t2 = n (the paper's n is the skinny width, k here).
+    for k in (2, 4, 8, 16):
+        r = pm.optimize_tiles(K40C, 10240, 10240, k, 8, latency_mem=latency_mem, latency_comp=8, c_setup=c_setup)
+        assert r.bound == "memory" and r.t2 == k, (k, r)
+        assert isinstance(r.t3, int) and 1 <= r.t3 <= 64
+
+
+@pytest.mark.parametrize("latency_comp", [4, 16, 64, 256])
+def test_alg7_m40_favours_computing(latency_comp):
+    # Sec. 4.2.2: M40 at n = 16 (double) is compute-bound and the procedure
+    # output compute-favouring parameters (printed t2 = 8): the compute
+    # branch, t2 between the threshold (~6) and 16.
+    r = pm.optimize_tiles(M40, 10240, 10240, 16, 8, latency_mem=400, latency_comp=latency_comp, c_setup=16)
+    thr = pm.t2_threshold(M40.peak_gflops, M40.bw_gbs, 8)
+    assert r.bound == "compute"
+    assert round(thr) <= r.t2 <= 16
+    # its time is the compute floor: 2 m n k operations at the peak or slower
+    assert r.time_s >= 2.0 * 10240 * 10240 * 16 / (M40.peak_gflops * 1e9) * (1 - 1e-12)
+
+
+def test_alg7_box_rounding_and_branch_rule():
+    import itertools
+    for peak, bw, k in itertools.product((100.0, 1000.0, 20000.0), (100.0, 900.0, 8000.0), (1, 3, 7, 16, 32)):
+        g = pm.Gpu("x", peak, bw, sms=80, clock_ghz=1.5, regs_per_sm=65536, smem_per_sm=100000, hw_max_threads=2048)
+        r = pm.optimize_tiles(g, 4096, 4096, k, 4, latency_mem=500, latency_comp=16, c_setup=8)
+        assert isinstance(r.t2, int) and isinstance(r.t3, int)
+        assert 1 <= r.t2 <= k and 1 <= r.t3 <= 64
+        thr = pm.t2_threshold(peak, bw, 4)
+        if k <= thr:
+            assert r.bound == "memory"
+        # the reported time is the larger of the choice's memory and compute times
+        tm = pm.mem_time(g, 4096, 4096, k, r.t2, r.t3, 4, 500, 8)
+        tc = pm.comp_time(g, 4096, 4096, k, r.t2, r.t3, 4, 16, 8)
+        assert abs(r.time_s - max(tm, tc)) <= 1e-12 * max(tm, tc)
+
+
+def test_util_comp_littles_law():
+    g = pm.Gpu("x", 1000.0, 100.0, sms=10, clock_ghz=1.0, regs_per_sm=65536, smem_per_sm=0, hw_max_threads=1024)
+    # need = latency * Peak / (#SM * clock) = 20 * 1000 / 10 = 2000 operations in flight per SM
+    occ = pm.max_occupancy(g, 2, 1, 4)
+    assert abs(pm.util_comp(g, 2, 1, 4, 20.0) - min(1.0, occ * 2 * 1 / 2000.0)) < 1e-12
+    assert pm.util_comp(g, 16, 8, 4, 20.0) == 1.0
